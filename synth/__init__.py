@@ -1,0 +1,128 @@
+"""Seeded synthetic inputs shared by the oracle side and the GPU side.
+
+This module only draws random numbers and writes them in the F-engine's
+sample format; it holds none of the X-engine's arithmetic (no unpacking, no
+products, no accumulation).  Both the tests and the benchmark feed the same
+bytes from here to the CPU oracle and to the CUDA library.
+
+Recipe (stand-in for LWA-SV F-engine output, which is not available here):
+
+* every complex sample has real and imaginary parts drawn from N(0, sigma^2)
+  with sigma = 2;
+* a common tone of amplitude 3 and frequency 0.05 cycles/sample is added to
+  every input of one channel (channel 10 by default), with per-input phase
+  phi_i = 0 or phi_i ~ U[0, 2 pi);
+* both parts are rounded half-to-even, clipped to [-8, 7] and stored as one
+  byte: real part in the high nibble, imaginary part in the low nibble, each
+  as 4-bit two's complement (section "Packet capture implementation");
+* the layout is uint8[T][C][N] -- time slowest, input fastest -- as the
+  capture block delivers a gulp of packets (channels x inputs per time).
+
+Time is drawn in blocks of ``_TBLOCK`` rows, each from its own child of
+``numpy.random.SeedSequence(seed)``, so the result is identical whatever the
+number of worker threads.
+"""
+from __future__ import annotations
+
+import hashlib
+import os
+from concurrent.futures import ThreadPoolExecutor
+
+import numpy as np
+
+_TBLOCK = 64
+
+
+def _nibble(v: np.ndarray) -> np.ndarray:
+    """int in [-8, 7] -> its 4-bit two's-complement code (0..15)."""
+    return (v.astype(np.int16) & 0xF).astype(np.uint8)
+
+
+def pack(re: np.ndarray, im: np.ndarray) -> np.ndarray:
+    """Encode integer parts in [-8, 7] as 4+4-bit bytes (re high, im low)."""
+    re = np.asarray(re)
+    im = np.asarray(im)
+    if re.shape != im.shape:
+        raise ValueError("re and im must have the same shape")
+    if re.size and (re.min() < -8 or re.max() > 7 or im.min() < -8 or im.max() > 7):
+        raise ValueError("components must lie in [-8, 7]")
+    return (_nibble(re) << 4) | _nibble(im)
+
+
+def _phases(seed: int, ninput: int, random_phase: bool) -> np.ndarray:
+    if not random_phase:
+        return np.zeros(ninput, dtype=np.float64)
+    rng = np.random.default_rng(np.random.SeedSequence([seed, 0x70A5E]))
+    return rng.uniform(0.0, 2.0 * np.pi, size=ninput)
+
+
+def voltages(ninput: int, nchan: int, ntime: int, seed: int, *,
+             sigma: float = 2.0, tone_chan: int | None = 10,
+             tone_amp: float = 3.0, tone_freq: float = 0.05,
+             random_phase: bool = False, threads: int | None = None,
+             t0: int = 0) -> np.ndarray:
+    """One gulp of 4+4-bit voltages, uint8[ntime][nchan][ninput].
+
+    ``t0`` offsets the time index of the tone, so consecutive gulps of a
+    stream continue the same sinusoid.
+    """
+    if min(ninput, nchan, ntime) < 0:
+        raise ValueError("sizes must be non-negative")
+    out = np.empty((ntime, nchan, ninput), dtype=np.uint8)
+    if out.size == 0:
+        return out
+    phi = _phases(seed, ninput, random_phase)
+    nblk = (ntime + _TBLOCK - 1) // _TBLOCK
+    children = np.random.SeedSequence([seed, t0]).spawn(nblk)
+    use_tone = tone_chan is not None and 0 <= tone_chan < nchan and tone_amp != 0
+
+    def fill(b: int) -> None:
+        ta, tb = b * _TBLOCK, min(ntime, (b + 1) * _TBLOCK)
+        rng = np.random.default_rng(children[b])
+        shape = (tb - ta, nchan, ninput)
+        re = rng.standard_normal(shape, dtype=np.float32) * np.float32(sigma)
+        im = rng.standard_normal(shape, dtype=np.float32) * np.float32(sigma)
+        if use_tone:
+            t = np.arange(ta + t0, tb + t0, dtype=np.float64)[:, None]
+            ang = 2.0 * np.pi * tone_freq * t + phi[None, :]
+            re[:, tone_chan, :] += (tone_amp * np.cos(ang)).astype(np.float32)
+            im[:, tone_chan, :] += (tone_amp * np.sin(ang)).astype(np.float32)
+        rq = np.clip(np.rint(re), -8, 7).astype(np.int8)
+        iq = np.clip(np.rint(im), -8, 7).astype(np.int8)
+        out[ta:tb] = (_nibble(rq) << 4) | _nibble(iq)
+
+    if threads is None:
+        threads = min(32, len(os.sched_getaffinity(0)))
+    if threads <= 1 or nblk == 1:
+        for b in range(nblk):
+            fill(b)
+    else:
+        with ThreadPoolExecutor(max_workers=threads) as ex:
+            list(ex.map(fill, range(nblk)))
+    return out
+
+
+def uniform_bytes(shape, seed: int) -> np.ndarray:
+    """Uniformly random packed bytes (every nibble value equally likely)."""
+    rng = np.random.default_rng(seed)
+    return rng.integers(0, 256, size=shape, dtype=np.uint8)
+
+
+def sha256(x: np.ndarray) -> str:
+    """Content hash of an input array, for caching oracle results."""
+    return hashlib.sha256(np.ascontiguousarray(x).tobytes()).hexdigest()
+
+
+# Workloads (N inputs, C channels, T samples per integration), with the seed
+# and phase rule of each.
+CONFIGS = {
+    "tiny": dict(ninput=16, nchan=64, ntime=1024, seed=1, random_phase=False),
+    "lwa": dict(ninput=512, nchan=256, ntime=8192, seed=2, random_phase=True),
+    "large_n": dict(ninput=2048, nchan=64, ntime=4096, seed=3, random_phase=True),
+}
+
+
+def config_voltages(name: str, **overrides) -> np.ndarray:
+    kw = dict(CONFIGS[name])
+    kw.update(overrides)
+    return voltages(**kw)
