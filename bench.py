@@ -1,0 +1,393 @@
+#!/usr/bin/env python
+"""Benchmark of the X-engine hot path on B300.
+
+One step = one pass of the whole path over one gulp already resident in HBM:
+correlate (unpack fused into the operand load, tcgen05 contraction, int32
+accumulate) + integrate (emit the packed lower triangle).  Default workload:
+512 inputs, 256 channels, 8192 samples per integration (the LWA-SV-scale
+correlator, 2.754e11 useful complex MACs per step).
+
+Prints ONE JSON line on rank 0.  Under torchrun every rank runs its own
+independent gulp (channels are independent, no data-path collective):
+weak scaling, value = all ranks' complex MACs / max-over-ranks time.
+
+    python bench.py [--steps K] [--warmup W] [--operand fp8|fp16|int32]
+                    [--workload lwa|large_n|tiny] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import synth  # noqa: E402
+
+WORKLOADS = {
+    "lwa": ("lwa", "LWA-scale correlator: 512 inputs, 256 channels, 8192 samples/integration"),
+    "large_n": ("large_n", "Large-N correlator: 2048 inputs, 64 channels, 4096 samples/integration"),
+    "tiny": ("tiny", "tiny correlator: 16 inputs, 64 channels, 1024 samples/integration"),
+}
+METRIC = "X-engine complex-MAC TOPS & % FP8 peak at 512 inputs vs plain int32 kernel"
+TC_SOURCES = ["paper_1708_00720_b300/csrc/xe_tc.cu", "paper_1708_00720_b300/csrc/xe_ptx.cuh"]
+
+
+def cmac(N: int, C: int, T: int) -> int:
+    """Useful complex MACs of one integration: lower triangle with autos."""
+    return C * T * N * (N + 1) // 2
+
+
+def source_hash(paths) -> str:
+    h = hashlib.sha256()
+    for p in paths:
+        with open(os.path.join(ROOT, p), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def measured_peaks() -> dict:
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return {"bf16": d["bf16_tflops"], "bf16_sustained": d["bf16_tflops_sustained"],
+                "hbm": d["hbm_gbs"], "source": "measured"}
+    return {"bf16": 1800.0, "bf16_sustained": 1400.0, "hbm": 6400.0, "source": "fallback"}
+
+
+def recorded_traffic(kernel_key: str):
+    """Per-launch DRAM bytes from the committed ncu summary, if it was taken on
+    the current kernel source; otherwise None."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as f:
+        rec = json.load(f).get(kernel_key)
+    if not rec or rec.get("source_hash") != source_hash(TC_SOURCES):
+        return None
+    return rec.get("dram_bytes_per_launch")
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self) -> dict:
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for l in self.lines:
+            parts = [p.strip() for p in l.split(",")]
+            if len(parts) < 7:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx = max(mx, float(parts[1]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[3:7]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx or None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if os.environ.get("XE_BENCH_BACKEND", "nccl") == "nccl" else "gloo"
+        dist.init_process_group(backend=backend)
+        pg = dist
+    return world, rank, local, pg
+
+
+def max_over_ranks(value: float, pg, device) -> float:
+    if pg is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(pg, device):
+    if pg is not None:
+        import torch
+        t = torch.zeros(1, device=device)
+        pg.all_reduce(t)
+
+
+def oracle_sample(workload: str, budget_s: float, threads: int):
+    """Time the oracle (as it stands) on a bounded channel subset of the
+    workload; returns (cmac_per_s, sample description, cores)."""
+    import oracle
+    cfg = dict(synth.CONFIGS[workload])
+    N, T = cfg["ninput"], cfg["ntime"]
+    per_chan = cmac(N, 1, T)
+    # aim at ~budget_s of CPU work assuming ~0.3 G cMAC/s per thread
+    nchan = max(1, min(cfg["nchan"], int(budget_s * 3e8 * threads / per_chan)))
+    nchan = max(nchan - nchan % threads, min(threads, cfg["nchan"]))
+    cfg["nchan"] = nchan
+    cfg["tone_chan"] = 0
+    x = synth.voltages(**cfg)
+    t0 = time.perf_counter()
+    oracle.correlate(x, nthreads=threads)
+    dt = time.perf_counter() - t0
+    return cmac(N, nchan, T) / dt, f"{nchan} of {synth.CONFIGS[workload]['nchan']} channels, " \
+        f"all {N*(N+1)//2} baselines, {T} samples ({dt:.1f} s)", min(threads, nchan)
+
+
+def run_reference(args):
+    """--impl reference: the CPU oracle, timed on the host cores."""
+    world, rank, local, pg = dist_setup()
+    if rank != 0:
+        return
+    import oracle
+    threads = oracle.default_threads()
+    wl = args.workload
+    cfg = dict(synth.CONFIGS[wl])
+    N, T = cfg["ninput"], cfg["ntime"]
+    per_chan = cmac(N, 1, T)
+    nchan = max(threads, min(cfg["nchan"], int(args.ref_step_s * 3e8 * threads / per_chan)))
+    nchan -= nchan % threads
+    nchan = max(1, min(nchan, cfg["nchan"]))
+    cfg["nchan"] = nchan
+    x = synth.voltages(**cfg)
+    for _ in range(args.warmup):
+        oracle.correlate(x[:, :min(nchan, threads)], nthreads=threads)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.correlate(x, nthreads=threads)
+        times.append(time.perf_counter() - t0)
+    ms = 1e3 * sum(times) / len(times)
+    value = cmac(N, nchan, T) / (ms * 1e-3) / 1e12
+    sample = f"{nchan} of {synth.CONFIGS[wl]['nchan']} channels per step, all baselines, {T} samples"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "cMAC TOPS",
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
+        "data": "synthetic", "config": {"workload": WORKLOADS[wl][1], "sample": sample},
+        "cpu_baseline": {"value": value, "unit": "cMAC TOPS", "cores": min(threads, nchan),
+                         "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "cMAC TOPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def run_ours(args):
+    import torch
+    world, rank, local, pg = dist_setup()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    from paper_1708_00720_b300 import xengine as xe
+
+    wl = args.workload
+    cfg = dict(synth.CONFIGS[wl])
+    cfg["seed"] = cfg["seed"] + 1000 * rank
+    N, C, T = cfg["ninput"], cfg["nchan"], cfg["ntime"]
+    x = synth.voltages(**cfg)
+    step_cmac = cmac(N, C, T)
+
+    eng = xe.XEngine(N, C, T, args.operand, "ci32")
+    gulp = torch.from_numpy(x).to(dev)
+    vis = eng.vis_empty(device=dev)
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        eng.correlate(gulp, stream=stream)
+        eng.integrate(vis, stream=stream)
+
+    for _ in range(max(args.warmup, 3)):
+        step()
+    torch.cuda.synchronize(dev)
+    eng.check()
+
+    # ---- timed region: K steps, CUDA events, clocks sampled meanwhile
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
+           torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
+    launches0 = xe.xe_plan_launch_count(eng.plan)
+    barrier(pg, dev)
+    torch.cuda.synchronize(dev)
+    with ClockSampler(local) as clk:
+        t_start = torch.cuda.Event(enable_timing=True)
+        t_end = torch.cuda.Event(enable_timing=True)
+        t_start.record(stream)
+        for k in range(args.steps):
+            ev[k][0].record(stream)
+            eng.correlate(gulp, stream=stream)
+            ev[k][1].record(stream)
+            eng.integrate(vis, stream=stream)
+            ev[k][2].record(stream)
+        t_end.record(stream)
+        torch.cuda.synchronize(dev)
+    barrier(pg, dev)
+    launches = xe.xe_plan_launch_count(eng.plan) - launches0
+    eng.check()
+    total_ms = t_start.elapsed_time(t_end)
+    kern_ms = statistics.mean(e[0].elapsed_time(e[1]) for e in ev)
+    total_ms = max_over_ranks(total_ms, pg, dev)
+    ms = total_ms / args.steps
+    value = world * step_cmac / (ms * 1e-3) / 1e12
+
+    # ---- plain int32 CUDA-core kernel on the same gulp
+    int32_line = None
+    if args.operand != "int32" and not args.skip_int32:
+        e32 = xe.XEngine(N, C, T, "int32", "ci32")
+        for _ in range(2):
+            e32.correlate(gulp, stream=stream)
+        torch.cuda.synchronize(dev)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        n32 = 3
+        a.record(stream)
+        for _ in range(n32):
+            e32.correlate(gulp, stream=stream)
+            e32.integrate(vis, stream=stream)
+        b.record(stream)
+        torch.cuda.synchronize(dev)
+        e32.check()
+        ms32 = a.elapsed_time(b) / n32
+        int32_line = {"value": step_cmac / (ms32 * 1e-3) / 1e12, "unit": "cMAC TOPS",
+                      "ms_per_step": ms32, "speedup_of_tensor_path": (step_cmac / (ms * 1e-3) / 1e12) /
+                      (step_cmac / (ms32 * 1e-3) / 1e12)}
+        e32.close()
+
+    # ---- end to end through the host-buffer C-ABI call
+    e2e = None
+    if not args.skip_e2e:
+        h_in = torch.from_numpy(x).pin_memory()
+        h_out = eng.vis_empty(device="cpu", pin_memory=True)
+        xe.xe_correlate_host(eng.plan, h_in, T, 0, h_out)
+        n_e2e = max(2, min(args.steps, 5))
+        barrier(pg, dev)
+        t0 = time.perf_counter()
+        for _ in range(n_e2e):
+            xe.xe_correlate_host(eng.plan, h_in, T, 0, h_out)
+        dt = (time.perf_counter() - t0) / n_e2e
+        dt = max_over_ranks(dt, pg, dev)
+        e2e = {"value": world * step_cmac / dt / 1e12, "unit": "cMAC TOPS",
+               "h2d_bytes_per_step": int(x.nbytes), "d2h_bytes_per_step": int(h_out.numel() * 4),
+               "ms_per_step": dt * 1e3}
+
+    peaks = measured_peaks()
+    flops_per_launch = 8 * step_cmac  # 4 real multiplies + 4 adds per complex MAC
+    achieved = flops_per_launch / (kern_ms * 1e-3) / 1e12
+    if args.operand == "fp8":
+        peak = 2 * peaks["bf16"]
+        peak_note = f"{peaks['source']} bf16 burst x 2 (nominal fp8/bf16 ratio)"
+        key = "xcorr_tc_fp8"
+    elif args.operand == "fp16":
+        peak = peaks["bf16"]
+        peak_note = f"{peaks['source']} bf16 burst (nominal fp16 = bf16 rate)"
+        key = "xcorr_tc_fp16"
+    else:
+        peak = None
+        peak_note = "CUDA-core path: no tensor peak"
+        key = "xcorr_cudacore"
+    roofline = {"bound": "tensor" if peak else "alu", "achieved": achieved, "peak": peak,
+                "unit": "TFLOP/s", "frac": (achieved / peak) if peak else None,
+                "traffic": recorded_traffic(key), "kernel": key, "kernel_ms": kern_ms,
+                "peak_source": peak_note,
+                "algorithmic_flops_per_launch": flops_per_launch}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.skip_cpu:
+        import oracle
+        v, sample, cores = oracle_sample(wl, args.cpu_budget_s, oracle.default_threads())
+        cpu = {"value": v / 1e12, "unit": "cMAC TOPS", "cores": cores, "kind": "oracle",
+               "sample": sample}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": "cMAC TOPS", "n_gpus": world,
+            "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": {"fp8": "e4m3", "fp16": "f16", "int32": "int8x4->int32"}[args.operand],
+            "data": "synthetic (seeded 4+4-bit Gaussian sigma=2 + tone, LWA-SV shapes)",
+            "config": {"workload": WORKLOADS[wl][1], "n_input": N, "n_chan": C, "ntime": T,
+                       "operand": args.operand, "output": "ci32 packed lower triangle",
+                       "l2": "inputs (%d MiB) exceed L2 (126 MB); no flush" % (x.nbytes >> 20),
+                       "parallelism": f"weak, {world} independent gulps"},
+            "pct_fp8_peak": (100.0 * achieved / (2 * peaks["bf16"])) if args.operand != "int32" else None,
+            "step_tflops": 8 * step_cmac * world / (ms * 1e-3) / 1e12,
+            "input_gbs": world * x.nbytes / (ms * 1e-3) / 1e9,
+            "roofline": roofline,
+            "int32_cudacore": int32_line,
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": launches,
+            "clocks": clk.summary(),
+        }
+        print(json.dumps(line), flush=True)
+    eng.close()
+    if pg is not None:
+        pg.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--operand", choices=["fp8", "fp16", "int32"], default="fp8")
+    ap.add_argument("--workload", choices=list(WORKLOADS), default="lwa")
+    ap.add_argument("--skip-e2e", action="store_true")
+    ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--skip-int32", action="store_true")
+    ap.add_argument("--cpu-budget-s", type=float, default=15.0)
+    ap.add_argument("--ref-step-s", type=float, default=10.0)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,187 @@
+/*
+ * xengine.h -- C ABI of the B300 (sm_103a) FX-correlator X-engine.
+ *
+ * The X-engine takes gulps of 4+4-bit complex voltages laid out as
+ * (time, channel, input) and, for every frequency channel c, accumulates the
+ * Hermitian visibility matrix
+ *
+ *     V_c[i][j] = sum_t x[t][c][i] * conj(x[t][c][j]),        i >= j,
+ *
+ * emitting the packed lower triangle.  The pieces come from arXiv 1708.00720
+ * (Bifrost): the sample format is the F-engine's 4+4-bit complex signed
+ * integers (section "Packet capture implementation"); the unpack, the
+ * accumulate and the linear-algebra product are the unpack block, the
+ * accumulate block (section "Some included blocks") and the linear-algebra
+ * module (section "Back end"); a gulp is the span of data a block reads
+ * from its ring buffer in one step (section "Memory management and ring
+ * buffers").
+ *
+ * Conventions shared by every call
+ * --------------------------------
+ *  - Sample byte: real part in the high nibble, imaginary part in the low
+ *    nibble, each 4-bit two's complement in [-8, 7] (0x80 = -8 + 0i,
+ *    0x0F = 0 - 1i).
+ *  - Gulp layout: uint8 x[ntime][n_chan][n_input], input fastest.  Element
+ *    (t, c, i) is at byte t*n_chan*n_input + c*n_input + i.
+ *  - Visibility layout: [n_chan][n_input*(n_input+1)/2] complex values,
+ *    channel slowest; baseline (i, j), i >= j, at i*(i+1)/2 + j; each value
+ *    is an (re, im) pair of int32 (XE_OUT_CI32) or float (XE_OUT_CF32).
+ *    Every value is an exact integer below 2^31 in magnitude (CI32) and below
+ *    2^24 for any integration the plan accepts, so CF32 is exact too.
+ *  - Pointers named d_* are CUDA device pointers on the plan's device; h_*
+ *    are host pointers (pinned memory gives full copy speed).  The caller
+ *    owns every buffer it passes and must keep it alive until the stream work
+ *    that uses it has completed.  The plan owns its accumulator and
+ *    workspace.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Device work is enqueued asynchronously on it; argument
+ *    checks happen synchronously on the host and a call that fails a check
+ *    enqueues nothing.
+ *  - Calls never throw and never abort; they return an xe_status.  After
+ *    XE_ERR_CUDA, xe_plan_last_error() holds the CUDA error text.
+ *  - A plan is not thread-safe: calls on one plan must be serialised by the
+ *    caller.  Different plans are independent.
+ */
+#ifndef XENGINE_H
+#define XENGINE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define XE_API __attribute__((visibility("default")))
+#else
+#define XE_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    XE_OK = 0,
+    XE_ERR_INVALID_ARG = 1,        /* null pointer, negative size, bad enum */
+    XE_ERR_ALIGNMENT = 2,          /* pointer not 16-byte aligned, or n_input % 16 != 0 */
+    XE_ERR_SHAPE = 3,              /* size beyond what the plan was created for */
+    XE_ERR_ACCUM_BOUND = 4,        /* integration would lose exactness (see xe_correlate) */
+    XE_ERR_NOMEM = 5,              /* device allocation failed */
+    XE_ERR_CUDA = 6,               /* a CUDA runtime/driver call failed */
+    XE_ERR_DEVICE_UNSUPPORTED = 7, /* current device is not sm_103 */
+    XE_ERR_TIMEOUT = 8,            /* a bounded device-side wait gave up */
+    XE_ERR_BUSY = 9                /* resource in use (serving layer) */
+} xe_status;
+
+/* Operand type the contraction runs in.  All three give identical, exact
+ * results; they differ only in speed.
+ *  XE_OPERAND_FP8_E4M3        tcgen05 tensor cores, kind::f8f6f4 (fastest)
+ *  XE_OPERAND_FP16            tcgen05 tensor cores, kind::f16
+ *  XE_OPERAND_INT32_CUDACORE  plain CUDA-core int8 dot products into int32
+ *                             (the comparison baseline) */
+typedef enum {
+    XE_OPERAND_FP8_E4M3 = 0,
+    XE_OPERAND_FP16 = 1,
+    XE_OPERAND_INT32_CUDACORE = 2
+} xe_operand;
+
+/* Element type of emitted visibilities. */
+typedef enum {
+    XE_OUT_CI32 = 0,   /* int32 (re, im) pairs */
+    XE_OUT_CF32 = 1    /* float (re, im) pairs, exact integers */
+} xe_out;
+
+typedef struct xe_plan *xe_plan_t;
+
+/* Largest number of time samples one integration may hold (from the last
+ * xe_reset or non-accumulating xe_correlate): every visibility is at most
+ * 128 per sample in magnitude, so 128 * samples must stay below 2^31 for the
+ * int32 accumulator (XE_OUT_CI32) and at most 2^24 for exact float32 output
+ * (XE_OUT_CF32).  Inside one gulp the tensor-core kernels keep every float32
+ * partial sum exact by splitting the gulp into launches of at most 32768
+ * samples (450 * 32768 < 2^24), each adding into the int32 accumulator. */
+#define XE_MAX_SAMPLES_CI32 16777215LL
+#define XE_MAX_SAMPLES_CF32 131072LL
+
+/*
+ * Create a plan on the current CUDA device for n_input inputs (n_input %
+ * 16 == 0, 16 <= n_input <= 8192), n_chan channels (>= 1) and gulps of at
+ * most max_ntime samples (>= 1).  Allocates the int32
+ * integration accumulator (n_chan * n_input*(n_input+1)/2 * 8 bytes),
+ * zeroes it, and sets the sample counter to 0.  On failure *out is NULL.
+ * Errors: XE_ERR_INVALID_ARG, XE_ERR_ALIGNMENT (n_input % 16), XE_ERR_NOMEM,
+ * XE_ERR_DEVICE_UNSUPPORTED, XE_ERR_CUDA.
+ */
+XE_API xe_status xe_plan_create(xe_plan_t *out, int n_input, int n_chan, int max_ntime,
+                         xe_operand op, xe_out out_type);
+
+/* Free the plan and its device memory (synchronises its device first).
+ * NULL is accepted and ignored. */
+XE_API xe_status xe_plan_destroy(xe_plan_t plan);
+
+/*
+ * Unpack (section "Some included blocks", unpack; the TBN pipeline's 4+4 to
+ * 8+8 conversion): d_ci8[k][0] = real, d_ci8[k][1] = imaginary part of
+ * d_packed[k], for k < ntime * n_chan * n_input.  d_packed must be 16-byte
+ * aligned.  Does not touch the accumulator.
+ */
+XE_API xe_status xe_unpack(xe_plan_t plan, const uint8_t *d_packed, int8_t *d_ci8,
+                    int ntime, void *stream);
+
+/*
+ * Correlate one gulp d_gulp[ntime][n_chan][n_input] (16-byte aligned) into
+ * the plan's accumulator: accumulate = 0 replaces the accumulator with this
+ * gulp's visibilities and sets the sample counter to ntime; accumulate = 1
+ * adds them and adds ntime to the counter (the accumulate block).
+ * ntime = 0 is allowed (adds nothing / zeroes the accumulator); d_gulp may
+ * then be NULL.
+ * Errors: XE_ERR_SHAPE (ntime > max_ntime), XE_ERR_ACCUM_BOUND (the
+ * integration would hold more than XE_MAX_SAMPLES_CI32 / _CF32 samples),
+ * XE_ERR_ALIGNMENT, XE_ERR_INVALID_ARG, XE_ERR_CUDA.  A rejected call
+ * changes neither the accumulator nor the counter.
+ */
+XE_API xe_status xe_correlate(xe_plan_t plan, const uint8_t *d_gulp, int ntime,
+                       int accumulate, void *stream);
+
+/* Emit the accumulator as visibilities into d_vis (layout above, element
+ * type = the plan's xe_out).  d_vis must be 8-byte aligned. */
+XE_API xe_status xe_integrate(xe_plan_t plan, void *d_vis, void *stream);
+
+/* Zero the accumulator and the sample counter. */
+XE_API xe_status xe_reset(xe_plan_t plan, void *stream);
+
+/* Time samples in the current integration (host-side counter). */
+XE_API xe_status xe_samples_integrated(xe_plan_t plan, long long *out);
+
+/*
+ * End-to-end call on HOST buffers: copies h_gulp[ntime][n_chan][n_input] to
+ * the device, correlates it (accumulate as in xe_correlate), emits the
+ * accumulator into h_vis and waits for completion.  Copies and compute are
+ * pipelined over time slices on the plan's internal streams.  The device
+ * staging buffers are allocated on first use and kept by the plan.
+ * Synchronous: returns once h_vis holds the result.
+ */
+XE_API xe_status xe_correlate_host(xe_plan_t plan, const uint8_t *h_gulp, int ntime,
+                            int accumulate, void *h_vis);
+
+/* Wait for all device work, then report whether any bounded device-side
+ * wait of this plan's kernels gave up since the last check
+ * (XE_ERR_TIMEOUT; the code is in xe_plan_last_error and is then cleared). */
+XE_API xe_status xe_plan_check(xe_plan_t plan);
+
+/* Number of kernel launches this plan has enqueued since creation. */
+XE_API xe_status xe_plan_launch_count(xe_plan_t plan, long long *out);
+
+/* Static text for a status code. */
+XE_API const char *xe_status_string(xe_status s);
+
+/* Text of the last CUDA error seen by the plan ("" if none).  Valid until
+ * the next call on the plan. */
+XE_API const char *xe_plan_last_error(xe_plan_t plan);
+
+/* Library version string. */
+XE_API const char *xe_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* XENGINE_H */

@@ -1,0 +1,45 @@
+// Internal interface between the C-ABI layer (xe_api.cu) and the kernels.
+// Not installed; the public interface is include/xengine.h.
+#pragma once
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+namespace xe {
+
+// Parameters of one tcgen05 X-engine launch.
+struct TcParams {
+  int N;                  // inputs
+  int C;                  // channels
+  int nt;                 // 128-input tiles per side, ceil(N / 128)
+  int units;              // C * nt (nt + 1) / 2 work units (channel, tile pair)
+  int nks;                // 32-sample steps, ceil(T / 32), T <= 32768
+  int accumulate;         // 1: add into acc; 0: overwrite
+  int32_t* acc;           // [C][N (N + 1) / 2][2] int32 accumulator
+  int* err;               // device error word (bit mask of timed-out waits)
+  unsigned long long timeout_ns;  // bound on every device-side wait
+};
+
+// Shared-memory bytes and block size of the tcgen05 kernel (eb = operand
+// bytes per element: 1 = e4m3, 2 = f16).
+int tc_smem_bytes(int eb);
+int tc_threads();
+
+// One launch of the tcgen05 X-engine over a gulp described by tmap (uint8,
+// dims {N, C, T}, box {128, 1, 32}).
+cudaError_t launch_xcorr_tc(int eb, const CUtensorMap* tmap, const TcParams& prm, int grid,
+                            cudaStream_t stream);
+
+// Plain CUDA-core correlator (int8 dot products into int32), the baseline.
+cudaError_t launch_xcorr_cudacore(const uint8_t* gulp, int T, int C, int N, int32_t* acc,
+                                  int accumulate, cudaStream_t stream);
+
+// 4+4 -> 8+8 unpack of n packed samples (n % 16 == 0 not required).
+cudaError_t launch_unpack(const uint8_t* packed, int8_t* out, long long n, cudaStream_t stream);
+
+// Emit the int32 accumulator as float pairs (exact integers).
+cudaError_t launch_emit_cf32(const int32_t* acc, float* out, long long n_pairs,
+                             cudaStream_t stream);
+
+}  // namespace xe

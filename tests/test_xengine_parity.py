@@ -1,0 +1,247 @@
+"""GPU X-engine vs the CPU oracle, element by element (bit-exact).
+
+Every operand path (tcgen05 e4m3, tcgen05 f16, CUDA-core int32) is called
+through the C ABI on the same seeded bytes the oracle reads.  Small cases
+are compared in full; the full-size workloads are compared on sampled
+baselines computed one by one by the oracle, plus properties that hold at
+any size.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+OPS = ["fp8", "fp16", "int32"]
+
+
+@pytest.fixture(scope="module")
+def xe():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1708_00720_b300 import xengine
+    return xengine
+
+
+def run(xe, x, operand, out="ci32", max_ntime=None):
+    import torch
+    T, C, N = x.shape
+    eng = xe.XEngine(N, C, max_ntime or max(T, 1), operand, out)
+    g = torch.from_numpy(np.ascontiguousarray(x)).cuda()
+    eng.correlate(g)
+    v = eng.integrate()
+    torch.cuda.synchronize()
+    eng.check()
+    assert eng.samples() == T
+    res = v.cpu().numpy()
+    eng.close()
+    if out == "cf32":
+        assert np.all(res == np.round(res))
+    return res.astype(np.int64)
+
+
+SMALL_SHAPES = [  # (N, C, T): tile-ragged inputs, time tails, single samples
+    (16, 64, 1024),   # the tiny workload's shape
+    (48, 3, 100),
+    (144, 2, 33),
+    (272, 2, 257),
+    (128, 1, 1),
+    (256, 5, 64),
+    (16, 1, 31),
+    (400, 1, 96),
+]
+
+
+@pytest.mark.parametrize("operand", OPS)
+@pytest.mark.parametrize("shape", SMALL_SHAPES, ids=lambda s: "x".join(map(str, s)))
+def test_small_full_parity(xe, operand, shape):
+    N, C, T = shape
+    x = synth.voltages(N, C, T, seed=N * 7 + C + T, random_phase=True)
+    np.testing.assert_array_equal(run(xe, x, operand), oracle.correlate(x))
+
+
+@pytest.mark.parametrize("operand", OPS)
+def test_tiny_workload(xe, operand):
+    x = synth.config_voltages("tiny")
+    np.testing.assert_array_equal(run(xe, x, operand), oracle.correlate(x))
+
+
+@pytest.mark.parametrize("operand", OPS)
+def test_uniform_bytes_every_nibble(xe, operand):
+    x = synth.uniform_bytes((300, 3, 160), seed=21)
+    np.testing.assert_array_equal(run(xe, x, operand), oracle.correlate(x))
+
+
+@pytest.mark.parametrize("operand", OPS)
+def test_extreme_values_long_gulp(xe, operand):
+    """Samples drawn from the corners of the 4-bit square over 32768 samples:
+    the largest float32 partial sums one tensor-core launch may hold."""
+    rng = np.random.default_rng(5)
+    corners = np.array([0x88, 0x77, 0x87, 0x78, 0x80, 0x08, 0x70, 0x07], dtype=np.uint8)
+    x = corners[rng.integers(0, len(corners), (32768, 2, 128))]
+    np.testing.assert_array_equal(run(xe, x, operand), oracle.correlate(x))
+
+
+@pytest.mark.parametrize("operand", OPS)
+def test_all_minus_eight(xe, operand):
+    x = np.full((32768, 1, 16), 0x88, dtype=np.uint8)
+    v = run(xe, x, operand)
+    assert (v[..., 0] == 128 * 32768).all() and (v[..., 1] == 0).all()
+
+
+@pytest.mark.parametrize("operand", ["fp8", "fp16"])
+def test_gulp_longer_than_one_launch(xe, operand):
+    x = synth.voltages(32, 2, 40000, seed=3)
+    np.testing.assert_array_equal(run(xe, x, operand), oracle.correlate(x))
+
+
+@pytest.mark.parametrize("operand", OPS)
+def test_accumulate_and_reset(xe, operand):
+    import torch
+    x = synth.voltages(144, 3, 500, seed=9, random_phase=True)
+    eng = xe.XEngine(144, 3, 300, operand)
+    g1 = torch.from_numpy(x[:300].copy()).cuda()
+    g2 = torch.from_numpy(x[300:].copy()).cuda()
+    eng.correlate(g1)
+    eng.correlate(g2, accumulate=True)
+    assert eng.samples() == 500
+    v = eng.integrate().cpu().numpy()
+    eng.check()
+    np.testing.assert_array_equal(v, oracle.correlate(x))
+    eng.correlate(g2)  # overwrite
+    np.testing.assert_array_equal(eng.integrate().cpu().numpy(), oracle.correlate(x[300:]))
+    eng.reset()
+    assert eng.samples() == 0
+    assert (eng.integrate().cpu().numpy() == 0).all()
+    eng.correlate(g1[:0], accumulate=True)  # empty gulp adds nothing
+    assert (eng.integrate().cpu().numpy() == 0).all()
+    eng.close()
+
+
+@pytest.mark.parametrize("operand", OPS)
+def test_cf32_output(xe, operand):
+    x = synth.voltages(64, 4, 200, seed=10)
+    np.testing.assert_array_equal(run(xe, x, operand, out="cf32"), oracle.correlate(x))
+
+
+def test_cf32_bound(xe):
+    import torch
+    T = xe.XE_MAX_SAMPLES_CF32
+    eng = xe.XEngine(16, 1, T, "fp8", "cf32")
+    g = torch.full((T, 1, 16), 0x88, dtype=torch.uint8, device="cuda")
+    eng.correlate(g)  # exactly at the bound: 128 * T = 2^24
+    v = eng.integrate().cpu().numpy()
+    eng.check()
+    assert (v[..., 0] == 2.0 ** 24).all() and (v[..., 1] == 0).all()
+    with pytest.raises(xe.XEngineError) as e:
+        eng.correlate(g[:1], accumulate=True)
+    assert e.value.status == xe.XE_ERR_ACCUM_BOUND
+    assert eng.samples() == T  # a rejected call changes nothing
+    eng.close()
+
+
+def test_ci32_bound(xe):
+    import torch
+    T = xe.XE_MAX_SAMPLES_CI32
+    eng = xe.XEngine(16, 1, T, "fp8", "ci32")
+    g = torch.full((T, 1, 16), 0x88, dtype=torch.uint8, device="cuda")
+    eng.correlate(g)
+    v = eng.integrate().cpu().numpy()
+    eng.check()
+    assert (v[..., 0] == 128 * T).all() and (v[..., 1] == 0).all()
+    with pytest.raises(xe.XEngineError) as e:
+        eng.correlate(g[:1], accumulate=True)
+    assert e.value.status == xe.XE_ERR_ACCUM_BOUND
+    eng.close()
+
+
+def test_shape_and_alignment_errors(xe):
+    import torch
+    eng = xe.XEngine(32, 2, 64, "fp8")
+    g = torch.zeros((65, 2, 32), dtype=torch.uint8, device="cuda")
+    with pytest.raises(xe.XEngineError) as e:
+        xe.xe_correlate(eng.plan, g, 65)
+    assert e.value.status == xe.XE_ERR_SHAPE
+    with pytest.raises(xe.XEngineError) as e:
+        xe.xe_correlate(eng.plan, g.data_ptr() + 1, 8)
+    assert e.value.status == xe.XE_ERR_ALIGNMENT
+    vis = torch.zeros(2 * 528 * 2 + 1, dtype=torch.int32, device="cuda")
+    with pytest.raises(xe.XEngineError) as e:
+        xe.xe_integrate(eng.plan, vis.data_ptr() + 4)
+    assert e.value.status == xe.XE_ERR_ALIGNMENT
+    eng.close()
+
+
+def test_unpack(xe):
+    import torch
+    x = np.concatenate([np.arange(256, dtype=np.uint8),
+                        synth.uniform_bytes(16 * 64 * 3 - 256, 3)]).reshape(3, 64, 16)
+    eng = xe.XEngine(16, 64, 3, "fp8")
+    g = torch.from_numpy(x).cuda()
+    out = torch.empty((3, 64, 16, 2), dtype=torch.int8, device="cuda")
+    xe.xe_unpack(eng.plan, g, out, 3)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(out.cpu().numpy(), oracle.unpack(x))
+    eng.close()
+
+
+def test_host_end_to_end(xe):
+    import torch
+    x = synth.voltages(256, 8, 5000, seed=12, random_phase=True)
+    eng = xe.XEngine(256, 8, 5000, "fp8")
+    h_in = torch.from_numpy(x).pin_memory()
+    h_out = eng.vis_empty(device="cpu", pin_memory=True)
+    xe.xe_correlate_host(eng.plan, h_in, 5000, 0, h_out)
+    eng.check()
+    np.testing.assert_array_equal(h_out.numpy(), oracle.correlate(x))
+    assert eng.samples() == 5000
+    eng.close()
+
+
+# ---------------------------------------------------------------- full size
+def sampled_check(v, x, rng, nsamp=1500):
+    T, C, N = x.shape
+    cs = rng.integers(0, C, nsamp)
+    ii = rng.integers(0, N, nsamp)
+    jj = (rng.random(nsamp) * (ii + 1)).astype(np.int64)
+    # always include the tile corners and the last input
+    extra = [(0, 0), (N - 1, 0), (N - 1, N - 1), (127, 127), (128, 127), (min(N - 1, 255), 128)]
+    for (i, j) in extra:
+        cs = np.append(cs, rng.integers(0, C))
+        ii = np.append(ii, i)
+        jj = np.append(jj, j)
+    for c, i, j in zip(cs, ii, jj):
+        want = oracle.correlate_one(x, int(c), int(i), int(j))
+        got = tuple(v[c, oracle.tri_index(int(i), int(j))])
+        assert got == want, (c, i, j, got, want)
+
+
+def properties_check(v, x):
+    T, C, N = x.shape
+    diag = np.array([oracle.tri_index(i, i) for i in range(N)])
+    assert (v[:, diag, 1] == 0).all()
+    assert (v[:, diag, 0] >= 0).all()
+    assert np.abs(v[..., 0]).max() <= 128 * T
+
+
+@pytest.mark.parametrize("operand", ["fp8", "int32"])
+def test_lwa_workload_sampled(xe, operand):
+    x = synth.config_voltages("lwa")
+    v = run(xe, x, operand)
+    properties_check(v, x)
+    sampled_check(v, x, np.random.default_rng(1))
+    # autocorrelations of a few channels in full
+    for c in (0, 10, 255):
+        for i in range(0, 512, 37):
+            assert tuple(v[c, oracle.tri_index(i, i)]) == oracle.correlate_one(x, c, i, i)
+
+
+@pytest.mark.parametrize("operand", ["fp8", "fp16"])
+def test_large_n_workload_sampled(xe, operand):
+    x = synth.config_voltages("large_n")
+    v = run(xe, x, operand)
+    properties_check(v, x)
+    sampled_check(v, x, np.random.default_rng(2))
