@@ -72,8 +72,10 @@ xe_status cuda_fail(xe_plan* p, cudaError_t e, const char* what) {
 
 bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
-// Encode the tensor map of one gulp slice: uint8 {N, C, T}, box {128, 1, 32}.
-xe_status encode_gulp_map(xe_plan* p, const uint8_t* gulp, int T, CUtensorMap* map) {
+// Encode the tensor map of one gulp slice: uint8 {N, C, T}; box {128, 1, 128}
+// with the 128-byte shared-memory swizzle (e4m3 kernel) or {128, 1, 32}
+// without (f16 kernel).
+xe_status encode_gulp_map(xe_plan* p, const uint8_t* gulp, int T, bool swizzle128, CUtensorMap* map) {
   EncodeTiledFn enc = get_encode_fn();
   if (!enc) {
     p->last_error = "cuTensorMapEncodeTiled entry point unavailable";
@@ -83,10 +85,12 @@ xe_status encode_gulp_map(xe_plan* p, const uint8_t* gulp, int T, CUtensorMap* m
                         static_cast<cuuint64_t>(T)};
   cuuint64_t strides[2] = {static_cast<cuuint64_t>(p->N),
                            static_cast<cuuint64_t>(p->N) * static_cast<cuuint64_t>(p->C)};
-  cuuint32_t box[3] = {128, 1, 32};
+  // e4m3 kernel: 4 steps (128 time rows) per box, see xe_tc8.cu; f16 kernel: 1 step
+  cuuint32_t box[3] = {128, 1, swizzle128 ? 128u : 32u};
   cuuint32_t estr[3] = {1, 1, 1};
   CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 3, const_cast<uint8_t*>(gulp), dims, strides,
-                   box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                   box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                   swizzle128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_NONE,
                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) {
     char buf[96];
@@ -121,19 +125,20 @@ xe_status enqueue_correlate(xe_plan* p, const uint8_t* d_gulp, int ntime, int ac
   for (int t0 = 0; t0 < ntime; t0 += kTcMaxLaunchNtime) {
     const int T = (ntime - t0) < kTcMaxLaunchNtime ? (ntime - t0) : kTcMaxLaunchNtime;
     CUtensorMap map;
-    xe_status st = encode_gulp_map(p, d_gulp + static_cast<size_t>(t0) * row_bytes, T, &map);
+    xe_status st = encode_gulp_map(p, d_gulp + static_cast<size_t>(t0) * row_bytes, T, eb == 1, &map);
     if (st != XE_OK) return st;
     xe::TcParams prm;
     prm.N = p->N;
     prm.C = p->C;
     prm.nt = nt;
     prm.units = static_cast<int>(units);
-    prm.nks = (T + 31) / 32;
+    prm.nks = (eb == 1) ? 4 * ((T + 127) / 128) : (T + 31) / 32;  // e4m3 kernel: whole 4-step TMA boxes
     prm.accumulate = (accumulate || t0 > 0) ? 1 : 0;
     prm.acc = p->d_acc;
     prm.err = p->d_err;
     prm.timeout_ns = kWaitTimeoutNs;
-    cudaError_t e = xe::launch_xcorr_tc(eb, &map, prm, grid, stream);
+    cudaError_t e = (eb == 1) ? xe::launch_xcorr_tc8(&map, prm, grid, stream)
+                              : xe::launch_xcorr_tc(eb, &map, prm, grid, stream);
     if (e != cudaSuccess) return cuda_fail(p, e, "tcgen05 launch");
     ++p->launches;
   }

@@ -38,11 +38,15 @@ __device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t by
                ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
 }
 
-__device__ __forceinline__ bool mbar_try_wait(uint32_t bar_addr, uint32_t parity) {
+// One test of the phase.  With a suspend-time hint the hardware parks the
+// thread until the phase completes (or the hint, in ns, expires), so waiting
+// warps do not spin on shared memory.
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar_addr, uint32_t parity,
+                                              uint32_t suspend_ns = 0x989680u) {
   uint32_t ok;
-  asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+  asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
                "selp.u32 %0, 1, 0, p;\n\t}"
-               : "=r"(ok) : "r"(bar_addr), "r"(parity) : "memory");
+               : "=r"(ok) : "r"(bar_addr), "r"(parity), "r"(suspend_ns) : "memory");
   return ok != 0;
 }
 
@@ -77,6 +81,13 @@ __device__ __forceinline__ void tma_load_3d(void* smem_dst, const void* desc, ui
       ::"r"(smem_u32(smem_dst)), "l"(reinterpret_cast<uint64_t>(desc)), "r"(smem_u32(bar)),
         "r"(x), "r"(y), "r"(z)
       : "memory");
+}
+
+// L2 prefetch of one tile of a 3-D tensor (no shared-memory destination).
+__device__ __forceinline__ void tma_prefetch_3d(const void* desc, int x, int y, int z) {
+  asm volatile("cp.async.bulk.prefetch.tensor.3d.L2.global.tile [%0, {%1, %2, %3}];"
+               ::"l"(reinterpret_cast<uint64_t>(desc)), "r"(x), "r"(y), "r"(z)
+               : "memory");
 }
 
 // ------------------------------------------------------------------ tcgen05

@@ -32,12 +32,14 @@
 // i.e. T' <= 37282 samples; the host splits longer gulps into launches of at
 // most 32768 samples that add into the int32 accumulator.
 //
-// Data path per CTA (one persistent CTA per SM, 384 threads):
+// Data path per CTA (one persistent CTA per SM, 512 threads):
 //   warp 0       TMA producer: raw 32 x 128-byte time x input tiles -> smem
 //   warp 1       MMA issuer (one thread): 4 tcgen05.mma per step
-//   warps 4..7   unpack: raw tile -> biased operand planes (MN-major, 128-byte
+//   warps 4..11  unpack, two groups of four warps taking alternate steps:
+//                raw tile -> biased operand planes (MN-major, 128-byte
 //                swizzle) + per-input sums
-//   warps 8..11  epilogue: tcgen05.ld of D, bias removal, int32 accumulate
+//   warps 12..15 epilogue: tcgen05.ld of D, bias removal, staging through
+//                shared memory, coalesced int32 accumulate
 // Accumulators are double-buffered in TMEM (2 x 256 columns) so a unit's
 // epilogue overlaps the next unit's MMAs.  All waits are bounded; on timeout
 // the kernel records an error code and returns.
@@ -55,26 +57,45 @@ namespace tc {
 constexpr int kTile = 128;           // inputs per tile side (MMA M and N)
 constexpr int kStep = 32;            // time samples per pipeline step
 constexpr int kRawTile = kStep * kTile;  // 4096 bytes of raw samples
-constexpr int kRawStages = 4;
-constexpr int kOpStages = 4;
-constexpr int kUnpackWarps = 4;
-constexpr int kUnpackThreads = kUnpackWarps * 32;
-constexpr int kEpiThreads = 128;
-constexpr int kThreads = 384;
+#ifndef XE_TC_UNPACK_GROUPS
+#define XE_TC_UNPACK_GROUPS 2
+#endif
+// Unpack warps form groups of four; group g converts the 32-sample steps
+// whose index is g modulo the number of groups, so consecutive steps are
+// unpacked concurrently.
+constexpr int kUnpackGroups = XE_TC_UNPACK_GROUPS;
+constexpr int kGroupThreads = 128;
 constexpr int kUnpackWarp0 = 4;
-constexpr int kEpiWarp0 = 8;
+constexpr int kUnpackWarps = 4 * kUnpackGroups;
+constexpr int kEpiWarp0 = kUnpackWarp0 + kUnpackWarps;  // a multiple of 4: one warp per TMEM lane quadrant
+constexpr int kEpiThreads = 128;
+constexpr int kThreads = 32 * (kEpiWarp0 + 4);
+constexpr int kEpiStagePitch = 33;  // int2 per staged row (32 + 1 pad)
 constexpr int kTmemCols = 512;       // 2 accumulator stages x (128 re + 128 im)
+
+#ifndef XE_TC_RAW_STAGES_F8
+#define XE_TC_RAW_STAGES_F8 12
+#endif
+#ifndef XE_TC_OP_STAGES_F8
+#define XE_TC_OP_STAGES_F8 4
+#endif
 
 template <int EB>  // operand bytes per element: 1 = e4m3, 2 = f16
 struct Cfg {
+  // Raw tiles in flight cover the L2/HBM latency of the TMA loads; operand
+  // stages decouple the unpack warps from the tensor pipe.
+  static constexpr int kRawStages = EB == 1 ? XE_TC_RAW_STAGES_F8 : 8;
+  static constexpr int kOpStages = EB == 1 ? XE_TC_OP_STAGES_F8 : 3;
   static constexpr int kPlane = kStep * kTile * EB;   // one re or im plane of one tile
   static constexpr int kOpStage = 4 * kPlane;         // I re, I im, J re, J im
   static constexpr int kRawStage = 2 * kRawTile;      // I raw, J raw
   static constexpr int kOpBytes = kOpStages * kOpStage;
   static constexpr int kRawBytes = kRawStages * kRawStage;
   static constexpr int kSumsBytes = 2 * 4 * kTile * 4;  // 2 stages x {P_I,Q_I,P_J,Q_J}[128] int
-  static constexpr int kBarOffset = kOpBytes + kRawBytes + kSumsBytes;
+  static constexpr int kEpiBytes = 4 * 32 * kEpiStagePitch * 8;  // per-warp 32 x 32 int2 staging
+  static constexpr int kBarOffset = kOpBytes + kRawBytes + kSumsBytes + kEpiBytes;
   static constexpr int kNumBars = 2 * kRawStages + 2 * kOpStages + 2 + 2 + 2 + 2 + 1;
+  static_assert(kBarOffset + kNumBars * 8 + 16 + 1024 <= 227 * 1024, "shared memory budget");
   static constexpr int kSmemBytes = kBarOffset + kNumBars * 8 + 16 + 1024;  // + align slack
 };
 
@@ -91,9 +112,10 @@ enum ErrCode : int {
 };
 
 struct SmemPtrs {
-  uint8_t* op;        // [kOpStages][4][kPlane]
-  uint8_t* raw;       // [kRawStages][2][kRawTile]
+  uint8_t* op;        // [Cfg::kOpStages][4][kPlane]
+  uint8_t* raw;       // [Cfg::kRawStages][2][kRawTile]
   int* sums;          // [2][4][kTile]
+  int2* epi;          // [4 warps][32][kEpiStagePitch]
   uint64_t* raw_full; uint64_t* raw_empty;
   uint64_t* op_full;  uint64_t* op_empty;
   uint64_t* acc_full; uint64_t* acc_empty;
@@ -110,11 +132,12 @@ __device__ __forceinline__ SmemPtrs carve(uint8_t* base) {
   p.op = base;
   p.raw = base + C::kOpBytes;
   p.sums = reinterpret_cast<int*>(base + C::kOpBytes + C::kRawBytes);
+  p.epi = reinterpret_cast<int2*>(base + C::kOpBytes + C::kRawBytes + C::kSumsBytes);
   uint64_t* b = reinterpret_cast<uint64_t*>(base + C::kBarOffset);
-  p.raw_full = b; b += kRawStages;
-  p.raw_empty = b; b += kRawStages;
-  p.op_full = b; b += kOpStages;
-  p.op_empty = b; b += kOpStages;
+  p.raw_full = b; b += C::kRawStages;
+  p.raw_empty = b; b += C::kRawStages;
+  p.op_full = b; b += C::kOpStages;
+  p.op_empty = b; b += C::kOpStages;
   p.acc_full = b; b += 2;
   p.acc_empty = b; b += 2;
   p.sums_full = b; b += 2;
@@ -279,19 +302,19 @@ xcorr_tc_kernel(const __grid_constant__ CUtensorMap tmap, TcParams prm) {
 
   // ---- set-up: barriers, TMEM, zeroed sums
   if (tid == 0) {
-    for (int k = 0; k < kRawStages; ++k) {
+    for (int k = 0; k < C::kRawStages; ++k) {
       mbar_init(&s.raw_full[k], 1);
-      mbar_init(&s.raw_empty[k], kUnpackThreads);
+      mbar_init(&s.raw_empty[k], 4);   // one elected lane per unpack warp of a group
     }
-    for (int k = 0; k < kOpStages; ++k) {
-      mbar_init(&s.op_full[k], kUnpackThreads);
+    for (int k = 0; k < C::kOpStages; ++k) {
+      mbar_init(&s.op_full[k], 4);
       mbar_init(&s.op_empty[k], 1);
     }
     for (int k = 0; k < 2; ++k) {
       mbar_init(&s.acc_full[k], 1);
-      mbar_init(&s.acc_empty[k], kEpiThreads);
-      mbar_init(&s.sums_full[k], kUnpackThreads);
-      mbar_init(&s.sums_empty[k], kEpiThreads);
+      mbar_init(&s.acc_empty[k], 4);
+      mbar_init(&s.sums_full[k], 4 * kUnpackGroups);
+      mbar_init(&s.sums_empty[k], 4);
     }
     mbar_init(s.final_bar, 1);
     *s.abort_flag = 0;
@@ -318,8 +341,8 @@ xcorr_tc_kernel(const __grid_constant__ CUtensorMap tmap, TcParams prm) {
         decode_unit(u, npairs, c, bi, bj);
         const bool diag = (bi == bj);
         for (int ks = 0; ks < nks; ++ks, ++it) {
-          const int st = it % kRawStages;
-          const uint32_t ph = (it / kRawStages) & 1;
+          const int st = it % C::kRawStages;
+          const uint32_t ph = (it / C::kRawStages) & 1;
           if (!wait_or_abort(&s.raw_empty[st], ph ^ 1, lim, abort_flag)) {
             fail(s, prm.err, kErrWaitRawEmpty);
             ok = false;
@@ -332,9 +355,9 @@ xcorr_tc_kernel(const __grid_constant__ CUtensorMap tmap, TcParams prm) {
         }
       }
       // wait for the copies still in flight (normally all consumed already)
-      for (int k = 0; k < kRawStages && k < it; ++k) {
+      for (int k = 0; k < C::kRawStages && k < it; ++k) {
         const int last = it - 1 - k;
-        mbar_wait(&s.raw_full[last % kRawStages], (last / kRawStages) & 1, lim);
+        mbar_wait(&s.raw_full[last % C::kRawStages], (last / C::kRawStages) & 1, lim);
       }
     }
   } else if (warp == 1) {
@@ -358,8 +381,8 @@ xcorr_tc_kernel(const __grid_constant__ CUtensorMap tmap, TcParams prm) {
         const uint32_t d_re = tmem + as * 256;
         const uint32_t d_im = d_re + 128;
         for (int ks = 0; ks < nks; ++ks, ++it) {
-          const int st = it % kOpStages;
-          const uint32_t ph = (it / kOpStages) & 1;
+          const int st = it % C::kOpStages;
+          const uint32_t ph = (it / C::kOpStages) & 1;
           if (!wait_or_abort(&s.op_full[st], ph, lim, abort_flag)) {
             fail(s, prm.err, kErrWaitOpFull);
             ok = false;
@@ -400,10 +423,11 @@ xcorr_tc_kernel(const __grid_constant__ CUtensorMap tmap, TcParams prm) {
     }
   } else if (warp >= kUnpackWarp0 && warp < kUnpackWarp0 + kUnpackWarps) {
     // ================================================= unpack
-    const int ut = tid - kUnpackWarp0 * 32;
+    const int grp = (warp - kUnpackWarp0) >> 2;
+    const int ut = tid - (kUnpackWarp0 + 4 * grp) * 32;
     const int q = ut & 7;         // 16-input column chunk
     const int r0 = ut >> 3;       // rows r0 and r0 + 16 of each 32-row step
-    int rit = 0, oit = 0, ui = 0;
+    int it = 0, ui = 0;
     bool ok = true;
     for (int u = blockIdx.x; u < prm.units && ok; u += gridDim.x, ++ui) {
       int c, bi, bj;
@@ -412,14 +436,16 @@ xcorr_tc_kernel(const __grid_constant__ CUtensorMap tmap, TcParams prm) {
       UnpackSums sI, sJ;
       sI.zero();
       sJ.zero();
-      for (int ks = 0; ks < nks; ++ks, ++rit, ++oit) {
-        const int rst = rit % kRawStages, ost = oit % kOpStages;
-        if (!wait_or_abort(&s.raw_full[rst], (rit / kRawStages) & 1, lim, abort_flag)) {
+      int since_flush = 0;
+      for (int ks = 0; ks < nks; ++ks, ++it) {
+        if (it % kUnpackGroups != grp) continue;
+        const int rst = it % C::kRawStages, ost = it % C::kOpStages;
+        if (!wait_or_abort(&s.raw_full[rst], (it / C::kRawStages) & 1, lim, abort_flag)) {
           fail(s, prm.err, kErrWaitRawFull);
           ok = false;
           break;
         }
-        if (!wait_or_abort(&s.op_empty[ost], ((oit / kOpStages) & 1) ^ 1, lim, abort_flag)) {
+        if (!wait_or_abort(&s.op_empty[ost], ((it / C::kOpStages) & 1) ^ 1, lim, abort_flag)) {
           fail(s, prm.err, kErrWaitOpEmpty);
           ok = false;
           break;
@@ -432,12 +458,18 @@ xcorr_tc_kernel(const __grid_constant__ CUtensorMap tmap, TcParams prm) {
           unpack_chunk<EB>(raw + kRawTile, op + 2 * C::kPlane, op + 3 * C::kPlane, r0, q, sJ);
           unpack_chunk<EB>(raw + kRawTile, op + 2 * C::kPlane, op + 3 * C::kPlane, r0 + 16, q, sJ);
         }
+        // each lane makes its operand writes visible to the tensor core, the
+        // warp converges, and one lane arrives for all 32
         fence_proxy_async_smem();
-        mbar_arrive(&s.op_full[ost]);
-        mbar_arrive(&s.raw_empty[rst]);
-        if ((ks & 7) == 7) {  // 16 rows per 8 steps: byte lanes stay <= 240
+        __syncwarp();
+        if (lane == 0) {
+          mbar_arrive(&s.op_full[ost]);
+          mbar_arrive(&s.raw_empty[rst]);
+        }
+        if (++since_flush == 8) {  // 16 rows per 8 steps: byte lanes stay <= 240
           sI.flush();
           sJ.flush();
+          since_flush = 0;
         }
       }
       if (!ok) break;
@@ -451,7 +483,8 @@ xcorr_tc_kernel(const __grid_constant__ CUtensorMap tmap, TcParams prm) {
       int* sums = s.sums + as * 4 * kTile;
       sI.publish(sums + 0 * kTile, sums + 1 * kTile, q);
       if (!diag) sJ.publish(sums + 2 * kTile, sums + 3 * kTile, q);
-      mbar_arrive(&s.sums_full[as]);
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&s.sums_full[as]);
     }
   } else if (warp >= kEpiWarp0) {
     // ================================================= epilogue
@@ -486,49 +519,58 @@ xcorr_tc_kernel(const __grid_constant__ CUtensorMap tmap, TcParams prm) {
         const int* PJ = diag ? sums : sums + 2 * kTile;
         const int* QJ = diag ? sums + kTile : sums + 3 * kTile;
         const int Pi = sums[r], Qi = sums[kTile + r];
-        const int gi = bi * kTile + r;
         const int row_re = -8 * (Pi + Qi) + 128 * T_pad;
         const int row_im = 8 * (Pi - Qi);
-        int32_t* out_row = prm.acc + 2 * (static_cast<long long>(c) * nbl +
-                                          static_cast<long long>(gi) * (gi + 1) / 2);
         const uint32_t t_row = tmem + (static_cast<uint32_t>(quad * 32) << 16) + as * 256;
+        int2* stg = s.epi + quad * 32 * kEpiStagePitch;
+        const long long chan_base = static_cast<long long>(c) * nbl;
 #pragma unroll 1
         for (int cc = 0; cc < kTile; cc += 32) {
           uint32_t vre[32], vim[32];
           tmem_ld32(t_row + cc, vre);
           tmem_ld32(t_row + 128 + cc, vim);
           tmem_ld_wait();
-          if (gi < prm.N) {
+          // this lane's row, 32 columns -> staging row `lane`
 #pragma unroll
-            for (int k = 0; k < 32; ++k) {
-              const int jl = cc + k;
-              const int gj = bj * kTile + jl;
-              if (gj <= gi && gj < prm.N) {
-                const int dre = __float2int_rn(__uint_as_float(vre[k]) * scale);
-                const int dim = __float2int_rn(__uint_as_float(vim[k]) * scale);
-                const int re = dre + row_re - 8 * (PJ[jl] + QJ[jl]);
-                const int im = dim + row_im - 8 * (PJ[jl] - QJ[jl]);
-                int2* dst = reinterpret_cast<int2*>(out_row + 2 * gj);
-                if (prm.accumulate) {
-                  const int2 o = *dst;
-                  *dst = make_int2(o.x + re, o.y + im);
-                } else {
-                  *dst = make_int2(re, im);
-                }
+          for (int k = 0; k < 32; ++k) {
+            const int jl = cc + k;
+            const int dre = __float2int_rn(__uint_as_float(vre[k]) * scale);
+            const int dim = __float2int_rn(__uint_as_float(vim[k]) * scale);
+            stg[lane * kEpiStagePitch + k] =
+                make_int2(dre + row_re - 8 * (PJ[jl] + QJ[jl]), dim + row_im - 8 * (PJ[jl] - QJ[jl]));
+          }
+          __syncwarp();
+          // row by row: 32 lanes write 32 consecutive baselines (256 bytes)
+          const int gj = bj * kTile + cc + lane;
+#pragma unroll 4
+          for (int rr = 0; rr < 32; ++rr) {
+            const int gr = bi * kTile + quad * 32 + rr;
+            if (gr < prm.N && gj <= gr && gj < prm.N) {
+              const int2 v = stg[rr * kEpiStagePitch + lane];
+              int2* dst = reinterpret_cast<int2*>(prm.acc) + chan_base +
+                          static_cast<long long>(gr) * (gr + 1) / 2 + gj;
+              if (prm.accumulate) {
+                const int2 o = *dst;
+                *dst = make_int2(o.x + v.x, o.y + v.y);
+              } else {
+                *dst = v;
               }
             }
           }
+          __syncwarp();
         }
         tc_fence_before();
       }
-      mbar_arrive(&s.acc_empty[as]);
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&s.acc_empty[as]);
       // every epilogue thread has read the column sums: clear this stage
       asm volatile("bar.sync 1, %0;" ::"n"(kEpiThreads) : "memory");
       sums[r] = 0;
       sums[kTile + r] = 0;
       sums[2 * kTile + r] = 0;
       sums[3 * kTile + r] = 0;
-      mbar_arrive(&s.sums_empty[as]);
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&s.sums_empty[as]);
     }
   }
 
