@@ -162,6 +162,36 @@ XE_API xe_status xe_samples_integrated(xe_plan_t plan, long long *out);
 XE_API xe_status xe_correlate_host(xe_plan_t plan, const uint8_t *h_gulp, int ntime,
                             int accumulate, void *h_vis);
 
+/*
+ * Allocation-free correlation of one gulp, for callers that cannot allocate
+ * device memory: a host framework that owns every device allocation through
+ * its own pool, or a real-time stream processor that reserves all of its
+ * memory at start-up and must not call cudaMalloc / cudaFree while observing.
+ * (The paper has no counterpart: this is a deployment convenience.)
+ *
+ * Same computation and result as a plan's xe_correlate(accumulate = 0)
+ * followed by xe_integrate, on the e4m3 tensor-core path: d_vis receives the
+ * visibilities of d_gulp[ntime][n_chan][n_input] (layout and element type as
+ * for xe_integrate).  No plan is needed and nothing is allocated: the int32
+ * scratch and the device error word live in a fixed 16 MiB + 256 B
+ * __device__ array of the library, which every GPU that loads the library
+ * keeps until the process exits.
+ *  - Limit: n_chan * n_input (n_input + 1) / 2 <= 2^21 complex values;
+ *    larger problems return XE_ERR_SHAPE without launching anything.
+ *  - ntime as for xe_correlate (XE_ERR_ACCUM_BOUND beyond XE_MAX_SAMPLES_*);
+ *    ntime = 0 writes zeros.  Same alignment rules as the plan calls.
+ *  - The first call on a device looks up the scratch's device address
+ *    (cudaGetSymbolAddress) with that device current; make that first call
+ *    before any stream capture.
+ *  - Every call shares the scratch and clears what must start at zero (the
+ *    error word); calls whose GPU work overlaps, e.g. on different streams,
+ *    race on it and must be serialised by the caller.
+ *  - Asynchronous on `stream`; errors as for the plan calls.
+ */
+XE_API xe_status xe_correlate_noalloc(const uint8_t *d_gulp, int ntime, int n_chan,
+                                      int n_input, xe_out out_type, void *d_vis,
+                                      void *stream);
+
 /* Wait for all device work, then report whether any bounded device-side
  * wait of this plan's kernels gave up since the last check
  * (XE_ERR_TIMEOUT; the code is in xe_plan_last_error and is then cleared). */
