@@ -39,7 +39,11 @@ WORKLOADS = {
     "tiny": ("tiny", "tiny correlator: 16 inputs, 64 channels, 1024 samples/integration"),
 }
 METRIC = "X-engine complex-MAC TOPS & % FP8 peak at 512 inputs vs plain int32 kernel"
-TC_SOURCES = ["paper_1708_00720_b300/csrc/xe_tc.cu", "paper_1708_00720_b300/csrc/xe_ptx.cuh"]
+KERNEL_SOURCES = {
+    "xcorr_tc_fp8": ["paper_1708_00720_b300/csrc/xe_tc8.cu", "paper_1708_00720_b300/csrc/xe_ptx.cuh"],
+    "xcorr_tc_fp16": ["paper_1708_00720_b300/csrc/xe_tc.cu", "paper_1708_00720_b300/csrc/xe_ptx.cuh"],
+    "xcorr_cudacore": ["paper_1708_00720_b300/csrc/xe_cudacore.cu"],
+}
 
 
 def cmac(N: int, C: int, T: int) -> int:
@@ -73,13 +77,13 @@ def recorded_traffic(kernel_key: str):
         return None
     with open(path) as f:
         rec = json.load(f).get(kernel_key)
-    if not rec or rec.get("source_hash") != source_hash(TC_SOURCES):
+    if not rec or rec.get("source_hash") != source_hash(KERNEL_SOURCES[kernel_key]):
         return None
     return rec.get("dram_bytes_per_launch")
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+    """nvidia-smi clocks and throttle reasons sampled every 50 ms."""
 
     FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
               "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
@@ -94,7 +98,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "50"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
@@ -162,24 +166,32 @@ def barrier(pg, device):
         pg.all_reduce(t)
 
 
-def oracle_sample(workload: str, budget_s: float, threads: int):
-    """Time the oracle (as it stands) on a bounded channel subset of the
-    workload; returns (cmac_per_s, sample description, cores)."""
-    import oracle
+def oracle_plan(workload: str, budget_s: float, threads: int):
+    """A bounded sample of the workload for the CPU oracle: one channel per
+    host thread and a leading slice of the integration, sized so the oracle
+    (about 5e7 complex MAC/s per thread) runs for roughly budget_s."""
     cfg = dict(synth.CONFIGS[workload])
-    N, T = cfg["ninput"], cfg["ntime"]
-    per_chan = cmac(N, 1, T)
-    # aim at ~budget_s of CPU work assuming ~0.3 G cMAC/s per thread
-    nchan = max(1, min(cfg["nchan"], int(budget_s * 3e8 * threads / per_chan)))
-    nchan = max(nchan - nchan % threads, min(threads, cfg["nchan"]))
-    cfg["nchan"] = nchan
-    cfg["tone_chan"] = 0
+    N, C, T = cfg["ninput"], cfg["nchan"], cfg["ntime"]
+    nchan = max(1, min(C, threads))
+    per_sample = nchan * N * (N + 1) // 2
+    ntime = int(budget_s * 5e7 * min(threads, nchan) / per_sample)
+    ntime = max(32, min(T, ntime - ntime % 32))
+    cfg.update(nchan=nchan, ntime=ntime, tone_chan=0)
+    sample = f"{nchan} of {C} channels x first {ntime} of {T} samples, all {N*(N+1)//2} baselines"
+    return cfg, sample
+
+
+def oracle_sample(workload: str, budget_s: float, threads: int):
+    """Time the oracle (as it stands) on a bounded sample of the workload;
+    returns (cmac_per_s, sample description, threads used)."""
+    import oracle
+    cfg, sample = oracle_plan(workload, budget_s, threads)
     x = synth.voltages(**cfg)
     t0 = time.perf_counter()
     oracle.correlate(x, nthreads=threads)
     dt = time.perf_counter() - t0
-    return cmac(N, nchan, T) / dt, f"{nchan} of {synth.CONFIGS[workload]['nchan']} channels, " \
-        f"all {N*(N+1)//2} baselines, {T} samples ({dt:.1f} s)", min(threads, nchan)
+    N, C, T = cfg["ninput"], cfg["nchan"], cfg["ntime"]
+    return cmac(N, C, T) / dt, f"{sample} ({dt:.1f} s)", min(threads, C)
 
 
 def run_reference(args):
@@ -190,30 +202,25 @@ def run_reference(args):
     import oracle
     threads = oracle.default_threads()
     wl = args.workload
-    cfg = dict(synth.CONFIGS[wl])
-    N, T = cfg["ninput"], cfg["ntime"]
-    per_chan = cmac(N, 1, T)
-    nchan = max(threads, min(cfg["nchan"], int(args.ref_step_s * 3e8 * threads / per_chan)))
-    nchan -= nchan % threads
-    nchan = max(1, min(nchan, cfg["nchan"]))
-    cfg["nchan"] = nchan
+    cfg, sample = oracle_plan(wl, args.ref_step_s, threads)
+    N, C, T = cfg["ninput"], cfg["nchan"], cfg["ntime"]
     x = synth.voltages(**cfg)
     for _ in range(args.warmup):
-        oracle.correlate(x[:, :min(nchan, threads)], nthreads=threads)
+        oracle.correlate(x[: max(32, T // 8)], nthreads=threads)
     times = []
     for _ in range(args.steps):
         t0 = time.perf_counter()
         oracle.correlate(x, nthreads=threads)
         times.append(time.perf_counter() - t0)
     ms = 1e3 * sum(times) / len(times)
-    value = cmac(N, nchan, T) / (ms * 1e-3) / 1e12
-    sample = f"{nchan} of {synth.CONFIGS[wl]['nchan']} channels per step, all baselines, {T} samples"
+    value = cmac(N, C, T) / (ms * 1e-3) / 1e12
+    sample = "per step: " + sample
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": "cMAC TOPS",
         "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int64",
         "data": "synthetic", "config": {"workload": WORKLOADS[wl][1], "sample": sample},
-        "cpu_baseline": {"value": value, "unit": "cMAC TOPS", "cores": min(threads, nchan),
+        "cpu_baseline": {"value": value, "unit": "cMAC TOPS", "cores": min(threads, C),
                          "kind": "oracle", "sample": sample},
         "e2e": {"value": value, "unit": "cMAC TOPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -230,6 +237,8 @@ def run_ours(args):
     wl = args.workload
     cfg = dict(synth.CONFIGS[wl])
     cfg["seed"] = cfg["seed"] + 1000 * rank
+    if args.nchan:
+        cfg["nchan"] = args.nchan  # smaller copies of a workload, for profiler captures
     N, C, T = cfg["ninput"], cfg["nchan"], cfg["ntime"]
     x = synth.voltages(**cfg)
     step_cmac = cmac(N, C, T)
@@ -349,7 +358,8 @@ def run_ours(args):
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             "dtype": {"fp8": "e4m3", "fp16": "f16", "int32": "int8x4->int32"}[args.operand],
             "data": "synthetic (seeded 4+4-bit Gaussian sigma=2 + tone, LWA-SV shapes)",
-            "config": {"workload": WORKLOADS[wl][1], "n_input": N, "n_chan": C, "ntime": T,
+            "config": {"workload": WORKLOADS[wl][1] + (f" (channels overridden: {C})" if args.nchan else ""),
+                       "n_input": N, "n_chan": C, "ntime": T,
                        "operand": args.operand, "output": "ci32 packed lower triangle",
                        "l2": "inputs (%d MiB) exceed L2 (126 MB); no flush" % (x.nbytes >> 20),
                        "parallelism": f"weak, {world} independent gulps"},
@@ -372,7 +382,7 @@ def run_ours(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--steps", type=int, default=300)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--operand", choices=["fp8", "fp16", "int32"], default="fp8")
@@ -380,8 +390,9 @@ def main():
     ap.add_argument("--skip-e2e", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--skip-int32", action="store_true")
+    ap.add_argument("--nchan", type=int, default=0, help="override the workload's channel count")
     ap.add_argument("--cpu-budget-s", type=float, default=15.0)
-    ap.add_argument("--ref-step-s", type=float, default=10.0)
+    ap.add_argument("--ref-step-s", type=float, default=3.0)
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
