@@ -126,3 +126,44 @@ def config_voltages(name: str, **overrides) -> np.ndarray:
     kw = dict(CONFIGS[name])
     kw.update(overrides)
     return voltages(**kw)
+
+
+# ---------------------------------------------------------------------------
+# gain-calibration inputs
+def gains(n_input: int, n_chan: int, seed: int, scatter: float = 0.1) -> np.ndarray:
+    """Complex gains g = 1 + scatter * CN(0, 1) per input and channel, [C][N]."""
+    rng = np.random.default_rng(np.random.SeedSequence([seed, 0x6A1]))
+    z = (rng.standard_normal((n_chan, n_input)) + 1j * rng.standard_normal((n_chan, n_input))) / np.sqrt(2)
+    return 1.0 + scatter * z
+
+
+def sky_model(n_input: int, n_chan: int, seed: int, n_sources: int = 5,
+              f_lo: float = 10e6, f_hi: float = 88e6) -> np.ndarray:
+    """Model visibilities of a random sky of point sources seen by an
+    LWA-SV-like station (section "LWA Sevilleta implementation": dipoles over
+    a 100 m x 110 m area, 10-88 MHz).  Input k is polarisation k % 2 of
+    antenna k // 2 and both polarisations share the antenna's position.
+    Fluxes U[1, 10], directions uniform in the unit disk, channels evenly
+    spaced in [f_lo, f_hi].  Returns complex128 [C][N(N+1)/2], packed lower
+    triangle: C_ij = sum_s S_s exp(-2 pi i nu/c ((x_i - x_j) l_s + (y_i - y_j) m_s))."""
+    rng = np.random.default_rng(np.random.SeedSequence([seed, 0x5C1]))
+    n_ant = (n_input + 1) // 2
+    x = rng.uniform(0.0, 100.0, n_ant)
+    y = rng.uniform(0.0, 110.0, n_ant)
+    flux = rng.uniform(1.0, 10.0, n_sources)
+    rad = np.sqrt(rng.uniform(0.0, 1.0, n_sources))
+    ang = rng.uniform(0.0, 2 * np.pi, n_sources)
+    l, m = rad * np.cos(ang), rad * np.sin(ang)
+    ant = np.arange(n_input) // 2
+    ii, jj = np.tril_indices(n_input)
+    dx = x[ant[ii]] - x[ant[jj]]
+    dy = y[ant[ii]] - y[ant[jj]]
+    nu = np.linspace(f_lo, f_hi, n_chan)
+    out = np.zeros((n_chan, len(ii)), dtype=np.complex128)
+    for s in range(n_sources):
+        phase = -2 * np.pi * (nu[:, None] / 299792458.0) * (dx[None, :] * l[s] + dy[None, :] * m[s])
+        out += flux[s] * np.exp(1j * phase)
+    return out
+
+
+CALIB_CONFIG = dict(n_input=512, n_chan=128, ntime=1024, seed=4)
