@@ -12,7 +12,11 @@ independent gulp (channels are independent, no data-path collective):
 weak scaling, value = all ranks' complex MACs / max-over-ranks time.
 
     python bench.py [--steps K] [--warmup W] [--operand fp8|fp16|int32]
-                    [--workload lwa|large_n|tiny] [--impl reference]
+                    [--workload lwa|large_n|tiny|calib] [--impl reference]
+
+--workload calib times the gain-calibration pass instead (chi^2 and its
+gradient in one HBM pass over V_obs, C and w; 512 inputs, 128 channels) and
+prints its own line with an HBM roofline.
 """
 from __future__ import annotations
 
@@ -37,7 +41,9 @@ WORKLOADS = {
     "lwa": ("lwa", "LWA-scale correlator: 512 inputs, 256 channels, 8192 samples/integration"),
     "large_n": ("large_n", "Large-N correlator: 2048 inputs, 64 channels, 4096 samples/integration"),
     "tiny": ("tiny", "tiny correlator: 16 inputs, 64 channels, 1024 samples/integration"),
+    "calib": ("calib", "gain calibration: chi^2 + gradient over 512 inputs x 128 channels of visibilities"),
 }
+CALIB_METRIC = "gain-calibration chi^2 + adjoint gradient: visibility baselines per second"
 METRIC = "X-engine complex-MAC TOPS & % FP8 peak at 512 inputs vs plain int32 kernel"
 KERNEL_SOURCES = {
     "xcorr_tc_fp8": ["paper_1708_00720_b300/csrc/xe_tc8.cu", "paper_1708_00720_b300/csrc/xe_ptx.cuh"],
@@ -194,15 +200,75 @@ def oracle_sample(workload: str, budget_s: float, threads: int):
     return cmac(N, C, T) / dt, f"{sample} ({dt:.1f} s)", min(threads, C)
 
 
+def calib_inputs(seed: int):
+    """Gains, sky model, observed visibilities (model x (1 + 30% scatter) +
+    complex Gaussian noise, sigma 2 per part) and unit weights, complex64 /
+    float32, for the 512-input 128-channel calibration workload."""
+    p = synth.CALIB_CONFIG
+    N, C = p["n_input"], p["n_chan"]
+    rng = np.random.default_rng(np.random.SeedSequence([seed, 0xCA1]))
+    nbl = N * (N + 1) // 2
+    g = synth.gains(N, C, seed).astype(np.complex64)
+    m = synth.sky_model(N, C, seed).astype(np.complex64)
+    noise = rng.standard_normal((C, nbl), dtype=np.float32) * np.float32(0.3)
+    v = m * (1 + noise) + 2 * (rng.standard_normal((C, nbl), dtype=np.float32) +
+                               1j * rng.standard_normal((C, nbl), dtype=np.float32))
+    w = np.ones((C, nbl), np.float32)
+    return N, C, g, m, v.astype(np.complex64), w
+
+
+def calib_bytes(N: int, C: int) -> int:
+    """Algorithmic bytes of one chi^2 + gradient pass: V, C (8 B) and w (4 B)
+    per baseline read once, g read and the gradient written (8 B each)."""
+    return 20 * C * N * (N + 1) // 2 + 16 * C * N
+
+
+def ref_step_budget(args) -> float:
+    """Seconds of oracle work per reference step: --ref-step-s, shrunk so that
+    warm-up plus K steps stay within about three minutes."""
+    return min(args.ref_step_s, max(0.05, 180.0 / max(1, args.steps + args.warmup)))
+
+
+def run_reference_calib(args):
+    from oracle import calib as ocal
+    N, C, g, m, v, w = calib_inputs(synth.CALIB_CONFIG["seed"])
+    nbl = N * (N + 1) // 2
+    nch = max(1, min(C, int(C * ref_step_budget(args) / 4.0)))   # ~4 s for all 128 channels
+    sl = slice(0, nch)
+    for _ in range(min(args.warmup, 1)):
+        ocal.chisq(g[sl][:1], m[sl][:1], v[sl][:1], w[sl][:1])
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        ocal.chisq(g[sl], m[sl], v[sl], w[sl])
+        ocal.grad(g[sl], m[sl], v[sl], w[sl])
+        times.append(time.perf_counter() - t0)
+    ms = 1e3 * sum(times) / len(times)
+    value = nch * nbl / (ms * 1e-3) / 1e9
+    sample = f"per step: {nch} of {C} channels, all {nbl} baselines, chi^2 then gradient (numpy float64, 1 thread)"
+    line = {
+        "impl": "reference", "metric": CALIB_METRIC, "value": value, "unit": "G baselines/s",
+        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": WORKLOADS["calib"][1], "sample": sample},
+        "cpu_baseline": {"value": value, "unit": "G baselines/s", "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "G baselines/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
 def run_reference(args):
     """--impl reference: the CPU oracle, timed on the host cores."""
     world, rank, local, pg = dist_setup()
     if rank != 0:
         return
+    if args.workload == "calib":
+        run_reference_calib(args)
+        return
     import oracle
     threads = oracle.default_threads()
     wl = args.workload
-    cfg, sample = oracle_plan(wl, args.ref_step_s, threads)
+    cfg, sample = oracle_plan(wl, ref_step_budget(args), threads)
     N, C, T = cfg["ninput"], cfg["nchan"], cfg["ntime"]
     x = synth.voltages(**cfg)
     for _ in range(args.warmup):
@@ -227,11 +293,123 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
+def run_calib(args, world, rank, local, pg, dev):
+    """One step = one xe_calib_chisq_grad call (chi^2 and the unscaled
+    gradient) over visibilities resident in HBM."""
+    import torch
+    from paper_1708_00720_b300 import calib
+    N, C, g, m, v, w = calib_inputs(synth.CALIB_CONFIG["seed"] + 1000 * rank)
+    nbl = N * (N + 1) // 2
+    dg, dm, dv, dw = (torch.from_numpy(a).to(dev) for a in (g, m, v, w))
+    cal = calib.Calibrator(N, C)
+    stream = torch.cuda.current_stream(dev)
+    chi_buf = torch.empty((), dtype=torch.float64, device=dev)
+    grad_buf = torch.empty_like(dg)
+    for _ in range(max(args.warmup, 3)):
+        cal.chisq_grad(dg, dm, dv, dw, True, stream=stream, chi_out=chi_buf, grad_out=grad_buf)
+    torch.cuda.synchronize(dev)
+    # One step captured as a CUDA graph (pass kernel + combine kernel) and
+    # replayed K times, so that the timed region is not paced by the Python
+    # binding's per-call overhead.
+    graph = torch.cuda.CUDAGraph()
+    cap = torch.cuda.Stream(dev)
+    cap.wait_stream(stream)
+    with torch.cuda.stream(cap):
+        graph.capture_begin()
+        cal.chisq_grad(dg, dm, dv, dw, True, stream=cap, chi_out=chi_buf, grad_out=grad_buf)
+        graph.capture_end()
+    stream.wait_stream(cap)
+    for _ in range(3):
+        graph.replay()
+    torch.cuda.synchronize(dev)
+    barrier(pg, dev)
+    torch.cuda.synchronize(dev)
+    with ClockSampler(local) as clk:
+        t_start = torch.cuda.Event(enable_timing=True)
+        t_end = torch.cuda.Event(enable_timing=True)
+        t_start.record(stream)
+        for k in range(args.steps):
+            graph.replay()
+        t_end.record(stream)
+        torch.cuda.synchronize(dev)
+    barrier(pg, dev)
+    call_ms = t_start.elapsed_time(t_end) / args.steps
+    total_ms = max_over_ranks(t_start.elapsed_time(t_end), pg, dev)
+    ms = total_ms / args.steps
+    value = world * C * nbl / (ms * 1e-3) / 1e9
+
+    # end to end: gains in from pinned host memory, chi^2 and gradient back
+    e2e = None
+    if not args.skip_e2e:
+        h_g = torch.from_numpy(g).pin_memory()
+        h_chi = torch.empty((), dtype=torch.float64).pin_memory()
+        h_grad = torch.empty((C, N), dtype=torch.complex64).pin_memory()
+        d_g = torch.empty_like(dg)
+
+        def host_step():
+            d_g.copy_(h_g, non_blocking=True)
+            chi, grad = cal.chisq_grad(d_g, dm, dv, dw, True, stream=stream, chi_out=chi_buf, grad_out=grad_buf)
+            h_chi.copy_(chi, non_blocking=True)
+            h_grad.copy_(grad, non_blocking=True)
+            torch.cuda.synchronize(dev)
+
+        host_step()
+        n_e2e = max(3, min(args.steps, 50))
+        barrier(pg, dev)
+        t0 = time.perf_counter()
+        for _ in range(n_e2e):
+            host_step()
+        dt = max_over_ranks((time.perf_counter() - t0) / n_e2e, pg, dev)
+        e2e = {"value": world * C * nbl / dt / 1e9, "unit": "G baselines/s",
+               "h2d_bytes_per_step": int(g.nbytes), "d2h_bytes_per_step": int(8 + g.nbytes),
+               "ms_per_step": dt * 1e3,
+               "note": "V_obs, C and w stay resident; per step the gains go in and chi^2 + gradient come back"}
+
+    peaks = measured_peaks()
+    nbytes = calib_bytes(N, C)
+    achieved = nbytes / (call_ms * 1e-3) / 1e9
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm"], "unit": "GB/s",
+                "frac": achieved / peaks["hbm"], "traffic": None, "kernel": "calib_pass_kernel<chi,grad>",
+                "kernel_ms": call_ms, "algorithmic_bytes_per_launch": nbytes,
+                "peak_source": f"{peaks['source']} HBM copy bandwidth",
+                "timed": "the whole step (pass kernel + combine kernel), graph replays, K steps / K"}
+    cpu = None
+    if rank == 0 and world == 1 and not args.skip_cpu:
+        from oracle import calib as ocal
+        nch = 32
+        t0 = time.perf_counter()
+        ocal.chisq(g[:nch], m[:nch], v[:nch], w[:nch])
+        ocal.grad(g[:nch], m[:nch], v[:nch], w[:nch])
+        dt = time.perf_counter() - t0
+        cpu = {"value": nch * nbl / dt / 1e9, "unit": "G baselines/s", "cores": 1, "kind": "oracle",
+               "sample": f"{nch} of {C} channels, all {nbl} baselines, chi^2 + gradient ({dt:.1f} s)"}
+    if rank == 0:
+        line = {
+            "metric": CALIB_METRIC, "value": value, "unit": "G baselines/s", "n_gpus": world,
+            "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32 (chi^2 sum f64)",
+            "data": "synthetic (seeded gains, 5-source sky model, noisy V_obs)",
+            "config": {"workload": WORKLOADS["calib"][1], "n_input": N, "n_chan": C, "weights": "ones (read)",
+                       "l2": f"inputs ({(m.nbytes + v.nbytes + w.nbytes) >> 20} MiB) exceed L2 (126 MB); no flush",
+                       "parallelism": f"weak, {world} independent problems"},
+            "hbm_gbs": nbytes * world / (ms * 1e-3) / 1e9,
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": 2 * args.steps, "clocks": clk.summary(),
+        }
+        print(json.dumps(line), flush=True)
+    cal.close()
+
+
 def run_ours(args):
     import torch
     world, rank, local, pg = dist_setup()
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
+    if args.workload == "calib":
+        run_calib(args, world, rank, local, pg, dev)
+        if pg is not None:
+            pg.destroy_process_group()
+        return
     from paper_1708_00720_b300 import xengine as xe
 
     wl = args.workload
@@ -382,7 +560,8 @@ def run_ours(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=300)
+    ap.add_argument("--steps", type=int, default=None,
+                    help="timed steps (default 300; 3000 for the calib workload, whose step is ~0.1 ms)")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--operand", choices=["fp8", "fp16", "int32"], default="fp8")
@@ -394,6 +573,10 @@ def main():
     ap.add_argument("--cpu-budget-s", type=float, default=15.0)
     ap.add_argument("--ref-step-s", type=float, default=3.0)
     args = ap.parse_args()
+    if args.steps is None:
+        args.steps = 3000 if (args.workload == "calib" and args.impl == "ours") else 300
+        if args.impl == "reference":
+            args.steps = 3
     if args.impl == "reference":
         run_reference(args)
     else:

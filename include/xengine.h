@@ -192,6 +192,57 @@ XE_API xe_status xe_correlate_noalloc(const uint8_t *d_gulp, int ntime, int n_ch
                                       int n_input, xe_out out_type, void *d_vis,
                                       void *stream);
 
+/* ------------------------------------------------------------------------
+ * Gain calibration on emitted visibilities (weighted chi^2 and its adjoint).
+ *
+ *   r_ij = V_ij - g_i conj(g_j) C_ij   for every channel c and baseline i >= j
+ *   chi2 = sum_c sum_{i>=j} w_ij |r_ij|^2           (i = j terms only if include_autos)
+ *   grad_k = dchi2/dRe g_k + i dchi2/dIm g_k
+ *          = -2 [ sum_{j<=k} w_kj r_kj g_j conj(C_kj) + sum_{i>=k} w_ik conj(r_ik) g_i C_ik ]
+ *
+ * Layouts (all device memory, interleaved (re, im) float32 pairs): d_g
+ * [n_chan][n_input]; d_model (C_ij) and d_vobs (V_ij) [n_chan][n_input *
+ * (n_input + 1) / 2] in the visibility layout above; d_w float32 weights in
+ * the same layout, or NULL for all ones.  Complex pointers must be 8-byte
+ * aligned.  Per-baseline terms are float32; chi^2 is summed in float64; both
+ * results are deterministic.  The object owns its scratch (per-CTA chi^2
+ * partials and the adjoint's partial sums); calls on one object must not
+ * overlap.  Errors: XE_ERR_INVALID_ARG for a NULL handle or required pointer
+ * or include_autos not 0/1, XE_ERR_ALIGNMENT for a misaligned pointer,
+ * XE_ERR_CUDA if a launch fails; nothing is launched on an error.
+ * (The paper's pipelines stop at the correlator; this is the calibration
+ * step that consumes its output.)
+ * ---------------------------------------------------------------------- */
+typedef struct xe_calib *xe_calib_t;
+
+/* n_input in 1..8192, n_chan in 1..2^20; allocates the scratch
+ * (about n_chan * n_input * (n_input / 4 + 8) bytes) on the current device. */
+XE_API xe_status xe_calib_create(xe_calib_t *out, int n_input, int n_chan);
+XE_API xe_status xe_calib_destroy(xe_calib_t calib);
+
+/* *d_chisq (one float64 in device memory) = chi2.  Asynchronous on stream. */
+XE_API xe_status xe_calib_chisq(xe_calib_t calib, const float *d_g, const float *d_model,
+                                const float *d_vobs, const float *d_w, int include_autos,
+                                double *d_chisq, void *stream);
+
+/* d_grad [n_chan][n_input] complex float32 = (*d_scale) * grad, d_scale a
+ * float64 in device memory (the incoming gradient of chi2) or NULL for 1. */
+XE_API xe_status xe_calib_grad(xe_calib_t calib, const float *d_g, const float *d_model,
+                               const float *d_vobs, const float *d_w, int include_autos,
+                               const double *d_scale, float *d_grad, void *stream);
+
+/* chi2 and the (unscaled) gradient from one pass over the visibilities: the
+ * same results as the two calls above, at half their memory traffic. */
+XE_API xe_status xe_calib_chisq_grad(xe_calib_t calib, const float *d_g, const float *d_model,
+                                     const float *d_vobs, const float *d_w, int include_autos,
+                                     double *d_chisq, float *d_grad, void *stream);
+
+/* d_out[k] = (*d_scale) * d_in[k] for the n_chan * n_input complex float32
+ * values of a gradient (d_in == d_out allowed); d_scale a float64 in device
+ * memory.  Applies an incoming gradient to a saved unscaled one. */
+XE_API xe_status xe_calib_scale(xe_calib_t calib, const float *d_in, const double *d_scale,
+                                float *d_out, void *stream);
+
 /* Wait for all device work, then report whether any bounded device-side
  * wait of this plan's kernels gave up since the last check
  * (XE_ERR_TIMEOUT; the code is in xe_plan_last_error and is then cleared). */

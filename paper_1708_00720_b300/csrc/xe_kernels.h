@@ -47,4 +47,15 @@ cudaError_t launch_unpack(const uint8_t* packed, int8_t* out, long long n, cudaS
 cudaError_t launch_emit_cf32(const int32_t* acc, float* out, long long n_pairs,
                              cudaStream_t stream);
 
+// Gain calibration (xe_calib.cu): persistent grid size; scratch bytes for
+// that grid; one pass (two launches) that computes chi^2 (if chisq !=
+// nullptr, float64 out), the gradient (if grad != nullptr, scaled by *scale
+// or 1), or both; and out = (*scale) * in.
+int calib_grid_ctas(int N, int C);
+size_t calib_scratch_bytes(int N, int C, int ctas);
+cudaError_t launch_calib(const float* g, const float* model, const float* vobs, const float* w, int N, int C,
+                         int ctas, int include_autos, void* scratch, double* chisq, const double* scale,
+                         float* grad, cudaStream_t stream);
+cudaError_t launch_calib_scale(const float* in, const double* scale, long long n, float* out, cudaStream_t stream);
+
 }  // namespace xe

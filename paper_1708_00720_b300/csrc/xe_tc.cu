@@ -64,7 +64,6 @@ constexpr int kRawTile = kStep * kTile;  // 4096 bytes of raw samples
 // whose index is g modulo the number of groups, so consecutive steps are
 // unpacked concurrently.
 constexpr int kUnpackGroups = XE_TC_UNPACK_GROUPS;
-constexpr int kGroupThreads = 128;
 constexpr int kUnpackWarp0 = 4;
 constexpr int kUnpackWarps = 4 * kUnpackGroups;
 constexpr int kEpiWarp0 = kUnpackWarp0 + kUnpackWarps;  // a multiple of 4: one warp per TMEM lane quadrant

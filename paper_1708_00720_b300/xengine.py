@@ -68,6 +68,12 @@ def _load() -> ctypes.CDLL:
         "xe_correlate_host": ([P, P, I, I, P], I),
         "xe_plan_check": ([P], I),
         "xe_plan_launch_count": ([P, ctypes.POINTER(LL)], I),
+        "xe_calib_create": ([ctypes.POINTER(P), I, I], I),
+        "xe_calib_destroy": ([P], I),
+        "xe_calib_chisq": ([P, P, P, P, P, I, P, P], I),
+        "xe_calib_grad": ([P, P, P, P, P, I, P, P, P], I),
+        "xe_calib_chisq_grad": ([P, P, P, P, P, I, P, P, P], I),
+        "xe_calib_scale": ([P, P, P, P, P], I),
         "xe_status_string": ([I], ctypes.c_char_p),
         "xe_plan_last_error": ([P], ctypes.c_char_p),
         "xe_version": ([], ctypes.c_char_p),

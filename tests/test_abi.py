@@ -65,3 +65,18 @@ def test_product_package_does_not_import_the_oracle():
         text = f.read_text()
         assert "import oracle" not in text and "from oracle" not in text, f
         assert "xcorr_oracle" not in text, f
+
+
+def test_calib_argument_checks_before_touching_the_device():
+    h = ctypes.c_void_p()
+    assert xe.status_of("xe_calib_create", ctypes.byref(h), 0, 4) == xe.XE_ERR_INVALID_ARG
+    assert xe.status_of("xe_calib_create", ctypes.byref(h), 8193, 4) == xe.XE_ERR_INVALID_ARG
+    assert xe.status_of("xe_calib_create", ctypes.byref(h), 16, 0) == xe.XE_ERR_INVALID_ARG
+    assert xe.status_of("xe_calib_create", None, 16, 4) == xe.XE_ERR_INVALID_ARG
+    P = ctypes.c_void_p
+    args = (P(16), P(16), P(16), None, 1)
+    assert xe.status_of("xe_calib_chisq", None, *args, P(16), None) == xe.XE_ERR_INVALID_ARG
+    assert xe.status_of("xe_calib_grad", None, *args, None, P(16), None) == xe.XE_ERR_INVALID_ARG
+    assert xe.status_of("xe_calib_chisq_grad", None, *args, P(16), P(16), None) == xe.XE_ERR_INVALID_ARG
+    assert xe.status_of("xe_calib_scale", None, P(16), P(16), P(16), None) == xe.XE_ERR_INVALID_ARG
+    assert xe.status_of("xe_calib_destroy", None) == xe.XE_OK
