@@ -243,6 +243,102 @@ XE_API xe_status xe_calib_chisq_grad(xe_calib_t calib, const float *d_g, const f
 XE_API xe_status xe_calib_scale(xe_calib_t calib, const float *d_in, const double *d_scale,
                                 float *d_out, void *stream);
 
+/* ------------------------------------------------------------------------
+ * Streaming service: several independent streams of gulps, each with a
+ * device ring, correlated and integrated as the gulps arrive (the paper's
+ * ring buffers, gulps, buffer factor and guaranteed / unguaranteed readers,
+ * section "Memory management and ring buffers" and "Guarantees").
+ *
+ * A writer (the capture side) reserves the next slot of a stream's pinned
+ * staging ring, fills it with one gulp uint8[gulp_ntime][n_chan][n_input],
+ * and commits it with its sequence number (strictly increasing; gaps are
+ * gulps that never arrived).  Committed gulps are copied to the device ring
+ * at once; pending gulps that are contiguous in the ring are correlated in
+ * one launch whenever the stream has fewer than two launches in flight.
+ * Integration k covers sequence numbers [k G, (k+1) G), G = integrate_gulps;
+ * it is emitted when its last gulp has been correlated, when a later gulp is
+ * committed, or on flush, into one of two pinned output buffers per stream
+ * that the consumer gets from xe_service_poll and hands back with
+ * xe_service_release.  Ring full: a guaranteed stream makes reserve wait (up
+ * to timeout_ms; back-pressure), an unguaranteed one returns XE_ERR_BUSY at
+ * once and counts the gulp as skipped.
+ *
+ * Admission: xe_service_add_stream returns XE_ERR_NOMEM when the stream's
+ * device memory (ring + accumulator + visibility buffer + 1 MiB) would take
+ * the service above its cap (mem_cap_bytes, or half the free device memory
+ * at creation when mem_cap_bytes <= 0).
+ *
+ * Calls on one service are thread-safe; each stream takes one writer and one
+ * consumer.  Errors: XE_ERR_INVALID_ARG (bad handle, id, sizes, sequence
+ * number), XE_ERR_ALIGNMENT (n_chan * n_input not a multiple of 16),
+ * XE_ERR_ACCUM_BOUND (integrate_gulps * gulp_ntime above the output type's
+ * sample bound), XE_ERR_NOMEM, XE_ERR_BUSY, XE_ERR_CUDA (a failed stream
+ * keeps returning it; other streams are unaffected).
+ * ---------------------------------------------------------------------- */
+typedef struct xe_service *xe_service_t;
+
+#define XE_SERVICE_DRYRUN 1  /* host bookkeeping only: no CUDA call, visibilities are zeros */
+#define XE_SERVICE_MANUAL 2  /* with DRYRUN: work stays in flight until xe_service_dryrun_complete */
+
+#define XE_FAULT_LAUNCH 1    /* the stream's next launch fails as a failing CUDA call would */
+#define XE_FAULT_DROP_GULP 2 /* the next committed gulp is lost in transit */
+
+typedef struct {
+  int n_input, n_chan;
+  int gulp_ntime;       /* samples per gulp */
+  int ring_gulps;       /* buffer factor: ring size in gulps, 1..1024 */
+  int integrate_gulps;  /* gulps per integration */
+  int guaranteed;       /* 1: back-pressure on a full ring; 0: skip */
+  int operand;          /* xe_operand */
+  int out_type;         /* xe_out */
+} xe_stream_config;
+
+typedef struct {
+  int stream;
+  long long index;      /* integration number k */
+  long long first_seq;  /* k * integrate_gulps */
+  int gulps;            /* gulps correlated into it */
+  int skipped;          /* integrate_gulps - gulps */
+  long long samples;    /* gulps * gulp_ntime */
+  double latency_ms;    /* commit of its last gulp -> visibilities in host memory */
+  const void *vis;      /* host [n_chan][n_input (n_input + 1) / 2] ci32 / cf32 pairs, valid until released */
+  long long vis_bytes;
+  int status;           /* XE_OK or the error that ended it */
+} xe_integration;
+
+typedef struct {
+  long long committed, skipped_full, dropped, launches, gulps_correlated, integrations, max_batch;
+  long long device_bytes, host_bytes;
+  int state;            /* XE_OK, or the error that stopped the stream */
+  int pending, inflight;
+} xe_stream_stats;
+
+XE_API xe_status xe_service_create(xe_service_t *out, long long mem_cap_bytes, int flags);
+XE_API xe_status xe_service_destroy(xe_service_t svc);   /* waits for the stream's work */
+XE_API xe_status xe_service_add_stream(xe_service_t svc, const xe_stream_config *cfg, int *stream_id);
+/* *h_slot = the next staging slot (gulp bytes, pinned host memory). */
+XE_API xe_status xe_service_reserve(xe_service_t svc, int stream, int timeout_ms, void **h_slot);
+XE_API xe_status xe_service_commit(xe_service_t svc, int stream, long long seq);
+/* reserve + copy from h_gulp + commit */
+XE_API xe_status xe_service_submit(xe_service_t svc, int stream, const void *h_gulp, long long seq,
+                                   int timeout_ms);
+/* Close the current integration even if gulps of it are missing. */
+XE_API xe_status xe_service_flush(xe_service_t svc, int stream);
+/* The oldest finished integration (XE_ERR_BUSY if none within timeout_ms). */
+XE_API xe_status xe_service_poll(xe_service_t svc, int stream, int timeout_ms, xe_integration *out);
+XE_API xe_status xe_service_release(xe_service_t svc, int stream, long long index);
+XE_API xe_status xe_service_stats(xe_service_t svc, int stream, xe_stream_stats *out);
+XE_API xe_status xe_service_inject(xe_service_t svc, int stream, int fault);   /* host-side fault injection */
+XE_API xe_status xe_service_dryrun_complete(xe_service_t svc, int stream);
+XE_API const char *xe_service_last_error(xe_service_t svc);
+
+/* Bounded device-side wait (failure detection): one thread waits until
+ * *d_flag == expected or timeout_ns (at most 60 s) passes, then writes
+ * *d_status = 0 (flag seen) or 1 (timed out) and the kernel ends; the
+ * context stays usable either way.  Asynchronous on stream. */
+XE_API xe_status xe_wait_flag(const int *d_flag, int expected, long long timeout_ns, int *d_status,
+                              void *stream);
+
 /* Wait for all device work, then report whether any bounded device-side
  * wait of this plan's kernels gave up since the last check
  * (XE_ERR_TIMEOUT; the code is in xe_plan_last_error and is then cleared). */

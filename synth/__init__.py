@@ -167,3 +167,18 @@ def sky_model(n_input: int, n_chan: int, seed: int, n_sources: int = 5,
 
 
 CALIB_CONFIG = dict(n_input=512, n_chan=128, ntime=1024, seed=4)
+
+
+# ---------------------------------------------------------------------------
+# streaming-service workload: three independent streams (N inputs, C
+# channels), gulps of 1024 samples, rings of 8 gulps, integrations of 8 gulps,
+# arriving at the LWA-SV cadence (1024 spectra x 40 us per gulp)
+SERVE_STREAMS = [
+    dict(ninput=256, nchan=64, seed=5),
+    dict(ninput=512, nchan=128, seed=6),
+    dict(ninput=1024, nchan=256, seed=7),
+]
+SERVE_GULP = 1024
+SERVE_RING = 8
+SERVE_INTEGRATE = 8
+SERVE_CADENCE_S = 1024 * 40e-6
