@@ -182,3 +182,29 @@ SERVE_GULP = 1024
 SERVE_RING = 8
 SERVE_INTEGRATE = 8
 SERVE_CADENCE_S = 1024 * 40e-6
+
+
+# ---------------------------------------------------------------------------
+# beamformer weights and workload
+def beam_weights(n_input: int, n_chan: int, n_beam: int, seed: int,
+                 f_lo: float = 10e6, f_hi: float = 88e6) -> np.ndarray:
+    """Phase-only weights steering beams to random directions (l, m) in the
+    unit disk for an LWA-SV-like station (dipoles in 100 m x 110 m, both
+    polarisations of an antenna at its position), channels evenly spaced in
+    [f_lo, f_hi]:  w[c][b][i] = exp(+2 pi i nu_c/c (x_i l_b + y_i m_b)) / N.
+    complex64 [C][B][N]."""
+    rng = np.random.default_rng(np.random.SeedSequence([seed, 0xBEA]))
+    n_ant = (n_input + 1) // 2
+    x = rng.uniform(0.0, 100.0, n_ant)
+    y = rng.uniform(0.0, 110.0, n_ant)
+    rad = np.sqrt(rng.uniform(0.0, 1.0, n_beam))
+    ang = rng.uniform(0.0, 2 * np.pi, n_beam)
+    l, m = rad * np.cos(ang), rad * np.sin(ang)
+    ant = np.arange(n_input) // 2
+    nu = np.linspace(f_lo, f_hi, n_chan)
+    ph = 2 * np.pi * (nu[:, None, None] / 299792458.0) * (x[ant][None, None, :] * l[None, :, None] +
+                                                          y[ant][None, None, :] * m[None, :, None])
+    return (np.exp(1j * ph) / n_input).astype(np.complex64)
+
+
+BEAM_CONFIG = dict(ninput=512, nchan=256, ntime=8192, nbeam=16, seed=8)
