@@ -42,9 +42,11 @@ WORKLOADS = {
     "large_n": ("large_n", "Large-N correlator: 2048 inputs, 64 channels, 4096 samples/integration"),
     "tiny": ("tiny", "tiny correlator: 16 inputs, 64 channels, 1024 samples/integration"),
     "calib": ("calib", "gain calibration: chi^2 + gradient over 512 inputs x 128 channels of visibilities"),
+    "beam": ("beam", "beamformer: 512 inputs, 256 channels, 8192 samples, 16 beams"),
     "serve": ("serve", "streaming service: 3 streams (256 x 64, 512 x 128, 1024 x 256 inputs x channels), "
                        "1024-sample gulps, rings of 8, integrations of 8"),
 }
+BEAM_METRIC = "4+4-bit beamformer: complex-MAC TOPS and input GB/s (% of HBM) at 512 inputs x 16 beams"
 SERVE_METRIC = ("streaming X-engine service, 3 streams: sustained aggregate cMAC TOPS at saturation "
                 "and gulp-to-visibility latency p50/p99")
 CALIB_METRIC = "gain-calibration chi^2 + adjoint gradient: visibility baselines per second"
@@ -233,6 +235,34 @@ def ref_step_budget(args) -> float:
     return min(args.ref_step_s, max(0.05, 180.0 / max(1, args.steps + args.warmup)))
 
 
+def run_reference_beam(args):
+    from oracle import beam as obeam
+    p = synth.BEAM_CONFIG
+    N, C, T, B = p["ninput"], p["nchan"], p["ntime"], p["nbeam"]
+    nt = max(16, min(T, int(170 * ref_step_budget(args))))   # ~170 samples per second of oracle time
+    x = synth.voltages(N, C, nt, seed=p["seed"], random_phase=True)
+    w = synth.beam_weights(N, C, B, seed=p["seed"])
+    for _ in range(min(args.warmup, 1)):
+        obeam.beamform(x[:16], w)
+    times = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        obeam.beamform(x, w)
+        times.append(time.perf_counter() - t0)
+    ms = 1e3 * sum(times) / len(times)
+    value = nt * C * N * B / (ms * 1e-3) / 1e12
+    sample = f"per step: first {nt} of {T} samples, all {C} channels, {B} beams (numpy einsum, complex128)"
+    line = {
+        "impl": "reference", "metric": BEAM_METRIC, "value": value, "unit": "cMAC TOPS", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOADS["beam"][1], "sample": sample},
+        "cpu_baseline": {"value": value, "unit": "cMAC TOPS", "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "cMAC TOPS", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
 def run_reference_calib(args):
     from oracle import calib as ocal
     N, C, g, m, v, w = calib_inputs(synth.CALIB_CONFIG["seed"])
@@ -268,6 +298,9 @@ def run_reference(args):
         return
     if args.workload == "calib":
         run_reference_calib(args)
+        return
+    if args.workload == "beam":
+        run_reference_beam(args)
         return
     import oracle
     threads = oracle.default_threads()
@@ -424,6 +457,111 @@ def link_peak_gbs(dev) -> tuple[float, float]:
     return best[0], best[1]
 
 
+def beam_bytes(N, C, T, B) -> int:
+    """Algorithmic bytes of one beamforming pass: the gulp (1 B per sample),
+    the beams (8 B per complex64 output) and the float16 operand weights."""
+    npad = -(-N // 64) * 64
+    return T * C * N + T * C * B * 8 + C * 2 * B * 2 * npad * 2
+
+
+def run_beam(args, world, rank, local, pg, dev):
+    """One step = one xe_beam_form over a resident gulp, captured in a CUDA
+    graph and replayed K times."""
+    import torch
+    from paper_1708_00720_b300 import beam as bmm
+    p = synth.BEAM_CONFIG
+    N, C, T, B = p["ninput"], p["nchan"], p["ntime"], p["nbeam"]
+    x = synth.voltages(N, C, T, seed=p["seed"] + 1000 * rank, random_phase=True)
+    w = synth.beam_weights(N, C, B, seed=p["seed"])
+    f = bmm.Beamformer(N, C, B, T)
+    f.set_weights(torch.from_numpy(w).to(dev))
+    gulp = torch.from_numpy(x).to(dev)
+    out = torch.empty((T, C, B), dtype=torch.complex64, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    for _ in range(max(args.warmup, 3)):
+        f.form(gulp, out, stream=stream)
+    torch.cuda.synchronize(dev)
+    f.check()
+    graph = torch.cuda.CUDAGraph()
+    cap = torch.cuda.Stream(dev)
+    cap.wait_stream(stream)
+    with torch.cuda.stream(cap):
+        graph.capture_begin()
+        f.form(gulp, out, stream=cap)
+        graph.capture_end()
+    stream.wait_stream(cap)
+    for _ in range(3):
+        graph.replay()
+    torch.cuda.synchronize(dev)
+    barrier(pg, dev)
+    torch.cuda.synchronize(dev)
+    with ClockSampler(local) as clk:
+        t_start = torch.cuda.Event(enable_timing=True)
+        t_end = torch.cuda.Event(enable_timing=True)
+        t_start.record(stream)
+        for _ in range(args.steps):
+            graph.replay()
+        t_end.record(stream)
+        torch.cuda.synchronize(dev)
+    barrier(pg, dev)
+    f.check()
+    call_ms = t_start.elapsed_time(t_end) / args.steps
+    ms = max_over_ranks(t_start.elapsed_time(t_end), pg, dev) / args.steps
+    cm = T * C * N * B
+    value = world * cm / (ms * 1e-3) / 1e12
+    nbytes = beam_bytes(N, C, T, B)
+    peaks = measured_peaks()
+    achieved = nbytes / (call_ms * 1e-3) / 1e9
+    e2e = None
+    if not args.skip_e2e:
+        h_in = torch.from_numpy(x).pin_memory()
+        h_out = torch.empty((T, C, B), dtype=torch.complex64).pin_memory()
+        d_in = torch.empty_like(gulp)
+
+        def host_step():
+            d_in.copy_(h_in, non_blocking=True)
+            f.form(d_in, out, stream=stream)
+            h_out.copy_(out, non_blocking=True)
+            torch.cuda.synchronize(dev)
+
+        host_step()
+        n_e2e = max(2, min(args.steps, 5))
+        barrier(pg, dev)
+        t0 = time.perf_counter()
+        for _ in range(n_e2e):
+            host_step()
+        dt = max_over_ranks((time.perf_counter() - t0) / n_e2e, pg, dev)
+        e2e = {"value": world * cm / dt / 1e12, "unit": "cMAC TOPS", "h2d_bytes_per_step": int(x.nbytes),
+               "d2h_bytes_per_step": int(h_out.numel() * 8), "ms_per_step": dt * 1e3}
+    cpu = None
+    if rank == 0 and world == 1 and not args.skip_cpu:
+        from oracle import beam as obeam
+        nt = 512
+        t0 = time.perf_counter()
+        obeam.beamform(x[:nt], w)
+        dt = time.perf_counter() - t0
+        cpu = {"value": nt * C * N * B / dt / 1e12, "unit": "cMAC TOPS", "cores": 1, "kind": "oracle",
+               "sample": f"first {nt} of {T} samples, all {C} channels and {B} beams, numpy einsum ({dt:.1f} s)"}
+    if rank == 0:
+        line = {
+            "metric": BEAM_METRIC, "value": value, "unit": "cMAC TOPS", "n_gpus": world,
+            "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f16 x biased-f16 -> f32",
+            "data": "synthetic (seeded 4+4-bit Gaussian sigma=2, phase-only steering weights)",
+            "config": {"workload": WORKLOADS["beam"][1], "n_input": N, "n_chan": C, "ntime": T, "n_beam": B,
+                       "l2": f"gulp ({x.nbytes >> 20} MiB) exceeds L2 (126 MB); no flush",
+                       "parallelism": f"weak, {world} independent gulps"},
+            "input_gbs": world * x.nbytes / (ms * 1e-3) / 1e9,
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm"], "unit": "GB/s",
+                         "frac": achieved / peaks["hbm"], "traffic": None, "kernel": "beam_kernel",
+                         "kernel_ms": call_ms, "algorithmic_bytes_per_launch": nbytes,
+                         "peak_source": f"{peaks['source']} HBM copy bandwidth"},
+            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": args.steps, "clocks": clk.summary(),
+        }
+        print(json.dumps(line), flush=True)
+    f.close()
+
+
 def run_serve(args, world, rank, local, pg, dev):
     """The streaming service under three loads: the LWA cadence, an offered
     rate sweep up to the knee, and saturation (writers never wait on a clock).
@@ -559,6 +697,11 @@ def run_ours(args):
     world, rank, local, pg = dist_setup()
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
+    if args.workload == "beam":
+        run_beam(args, world, rank, local, pg, dev)
+        if pg is not None:
+            pg.destroy_process_group()
+        return
     if args.workload == "serve":
         run_serve(args, world, rank, local, pg, dev)
         if pg is not None:
@@ -734,7 +877,7 @@ def main():
     ap.add_argument("--serve-gulps", type=int, default=64, help="gulps per stream in the saturation run")
     args = ap.parse_args()
     if args.steps is None:
-        args.steps = 3000 if (args.workload == "calib" and args.impl == "ours") else 300
+        args.steps = 3000 if (args.workload in ("calib", "beam") and args.impl == "ours") else 300
         if args.impl == "reference":
             args.steps = 3
     if args.impl == "reference":

@@ -339,6 +339,33 @@ XE_API const char *xe_service_last_error(xe_service_t svc);
 XE_API xe_status xe_wait_flag(const int *d_flag, int expected, long long timeout_ns, int *d_status,
                               void *stream);
 
+/* ------------------------------------------------------------------------
+ * Beamformer on 4+4-bit voltages (the DRX pipeline's phase-and-sum GPU
+ * beamformer, section "LWA Sevilleta implementation", which works directly
+ * on the 4+4-bit samples):  y[t][c][b] = sum_i w[c][b][i] x[t][c][i].
+ *
+ * d_w: complex64 (interleaved float pairs) weights [n_chan][n_beam][n_input]
+ * in device memory; xe_beam_set_weights converts them to float16 operand
+ * tiles (real and imaginary parts rounded to float16: the operand precision)
+ * and per-column bias sums held by the object.  xe_beam_form reads a gulp
+ * uint8[ntime][n_chan][n_input] (same layout as xe_correlate) and writes
+ * d_out complex64 [ntime][n_chan][n_beam]; products are accumulated in
+ * float32 on the tensor cores.  n_beam in 8..64, a multiple of 8; n_input
+ * a multiple of 16 (XE_ERR_ALIGNMENT otherwise); d_gulp and d_out 16-byte
+ * aligned.
+ * Asynchronous on stream; xe_beam_check reports XE_ERR_TIMEOUT if a bounded
+ * device wait gave up.  (The paper gives no beamformer algorithm beyond
+ * phase-and-sum; this is its definition.)
+ * ---------------------------------------------------------------------- */
+typedef struct xe_beam *xe_beam_t;
+
+XE_API xe_status xe_beam_create(xe_beam_t *out, int n_input, int n_chan, int n_beam, int max_ntime);
+XE_API xe_status xe_beam_destroy(xe_beam_t beam);
+XE_API xe_status xe_beam_set_weights(xe_beam_t beam, const float *d_w, void *stream);
+XE_API xe_status xe_beam_form(xe_beam_t beam, const uint8_t *d_gulp, int ntime, float *d_out, void *stream);
+XE_API xe_status xe_beam_check(xe_beam_t beam);
+XE_API const char *xe_beam_last_error(xe_beam_t beam);
+
 /* Wait for all device work, then report whether any bounded device-side
  * wait of this plan's kernels gave up since the last check
  * (XE_ERR_TIMEOUT; the code is in xe_plan_last_error and is then cleared). */

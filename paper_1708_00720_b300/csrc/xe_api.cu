@@ -101,6 +101,31 @@ xe_status encode_gulp_map(xe_plan* p, const uint8_t* gulp, int T, bool swizzle12
   return XE_OK;
 }
 
+}  // namespace
+
+// Tiled uint8 tensor map of rank 3 or 4 (no interleave, OOB reads as zeros),
+// shared with the beamformer.
+bool xe::encode_tensor_u8(CUtensorMap* map, const void* base, int rank, const unsigned long long* dims,
+                          const unsigned long long* strides, const unsigned* box, int swizzle_bytes) {
+  EncodeTiledFn enc = get_encode_fn();
+  if (!enc || rank < 1 || rank > 5) return false;
+  cuuint64_t d[5], st[4];
+  cuuint32_t bx[5], estr[5];
+  for (int i = 0; i < rank; ++i) {
+    d[i] = dims[i];
+    bx[i] = box[i];
+    estr[i] = 1;
+    if (i + 1 < rank) st[i] = strides[i];
+  }
+  return enc(map, CU_TENSOR_MAP_DATA_TYPE_UINT8, static_cast<cuuint32_t>(rank), const_cast<void*>(base), d, st, bx,
+             estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+             swizzle_bytes == 128 ? CU_TENSOR_MAP_SWIZZLE_128B
+                                  : swizzle_bytes == 64 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_NONE,
+             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+namespace {
+
 // Enqueue the correlation of one gulp (already validated) on `stream`.
 xe_status enqueue_correlate(xe_plan* p, const uint8_t* d_gulp, int ntime, int accumulate,
                             cudaStream_t stream) {

@@ -58,4 +58,31 @@ cudaError_t launch_calib(const float* g, const float* model, const float* vobs, 
                          float* grad, cudaStream_t stream);
 cudaError_t launch_calib_scale(const float* in, const double* scale, long long n, float* out, cudaStream_t stream);
 
+// Tiled uint8 tensor map of the given rank (dims innermost first, strides in
+// bytes of dims 1 .. rank-1), shared-memory swizzle of 0, 64 or 128 bytes,
+// OOB reads as zeros; false if encoding failed.
+bool encode_tensor_u8(CUtensorMap* map, const void* base, int rank, const unsigned long long* dims,
+                      const unsigned long long* strides, const unsigned* box, int swizzle_bytes);
+
+// Beamformer (xe_beam.cu).
+struct BeamParams {
+  int N, C, B;            // inputs, channels, beams
+  int S;                  // 64-input stages, ceil(N / 64)
+  int T;                  // samples in this launch
+  int tiles;              // 128-sample time tiles, ceil(T / 128)
+  const uint16_t* wt;     // [C][S][2][2B][64] float16 weights, K-major 128-byte-swizzled operand tiles
+  const float* bias;      // [C][2B] 8 * (sum of each operand row)
+  float* out;             // [T][C][B] complex64
+  int* err;               // device error word
+  unsigned long long timeout_ns;
+  int map4;               // 1: the raw map is 4-D {64, T, S, C} (box {64, 128, 4, 1}); 0: 3-D {N, C, T}
+                          // (box {64, 1, 128}); both with the 64-byte shared-memory swizzle
+};
+int beam_smem_bytes(int S, int B);
+int beam_threads();
+cudaError_t launch_beam(const CUtensorMap* tmap, const BeamParams& prm, int grid, cudaStream_t stream);
+int beam_w_group(int B);   // stages of weights per bulk copy
+cudaError_t launch_beam_weights(const float* w, int N, int C, int B, int S, uint16_t* wt, float* bias,
+                                cudaStream_t stream);
+
 }  // namespace xe
