@@ -55,6 +55,8 @@ KERNEL_SOURCES = {
     "xcorr_tc_fp8": ["paper_1708_00720_b300/csrc/xe_tc8.cu", "paper_1708_00720_b300/csrc/xe_ptx.cuh"],
     "xcorr_tc_fp16": ["paper_1708_00720_b300/csrc/xe_tc.cu", "paper_1708_00720_b300/csrc/xe_ptx.cuh"],
     "xcorr_cudacore": ["paper_1708_00720_b300/csrc/xe_cudacore.cu"],
+    "calib_pass": ["paper_1708_00720_b300/csrc/xe_calib.cu"],
+    "beam_kernel": ["paper_1708_00720_b300/csrc/xe_beam.cu", "paper_1708_00720_b300/csrc/xe_ptx.cuh"],
 }
 
 
@@ -407,7 +409,8 @@ def run_calib(args, world, rank, local, pg, dev):
     nbytes = calib_bytes(N, C)
     achieved = nbytes / (call_ms * 1e-3) / 1e9
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm"], "unit": "GB/s",
-                "frac": achieved / peaks["hbm"], "traffic": None, "kernel": "calib_pass_kernel<chi,grad>",
+                "frac": achieved / peaks["hbm"], "traffic": recorded_traffic("calib_pass"),
+                "kernel": "calib_pass_kernel<chi,grad>",
                 "kernel_ms": call_ms, "algorithmic_bytes_per_launch": nbytes,
                 "peak_source": f"{peaks['source']} HBM copy bandwidth",
                 "timed": "the whole step (pass kernel + combine kernel), graph replays, K steps / K"}
@@ -553,7 +556,8 @@ def run_beam(args, world, rank, local, pg, dev):
                        "parallelism": f"weak, {world} independent gulps"},
             "input_gbs": world * x.nbytes / (ms * 1e-3) / 1e9,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm"], "unit": "GB/s",
-                         "frac": achieved / peaks["hbm"], "traffic": None, "kernel": "beam_kernel",
+                         "frac": achieved / peaks["hbm"], "traffic": recorded_traffic("beam_kernel"),
+                         "kernel": "beam_kernel",
                          "kernel_ms": call_ms, "algorithmic_bytes_per_launch": nbytes,
                          "peak_source": f"{peaks['source']} HBM copy bandwidth"},
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": args.steps, "clocks": clk.summary(),
