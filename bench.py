@@ -803,9 +803,46 @@ def run_ours(args):
             xe.xe_correlate_host(eng.plan, h_in, T, 0, h_out)
         dt = (time.perf_counter() - t0) / n_e2e
         dt = max_over_ranks(dt, pg, dev)
-        e2e = {"value": world * step_cmac / dt / 1e12, "unit": "cMAC TOPS",
+        sync = {"value": world * step_cmac / dt / 1e12, "ms_per_step": dt * 1e3,
+                "api": "xe_correlate_host: one gulp in, its visibilities out, then the next"}
+        # Pipelined: consecutive gulps through the streaming service (one
+        # stream, an integration per gulp), so that the next gulp's
+        # host-to-device copy overlaps the previous result's copy back.
+        import threading
+        from paper_1708_00720_b300 import service as svm
+        svc = svm.Service()
+        R = 3
+        sid = svc.add_stream(N, C, T, ring_gulps=R, integrate_gulps=1, guaranteed=True, operand=args.operand)
+        for k in range(R):                      # the capture side writes each staging slot once
+            view = svc.reserve(sid, timeout_ms=60000)
+            view[...] = x
+            svc.commit(sid, k)
+        for k in range(R):
+            r = svc.poll(sid, timeout_ms=60000)
+            svc.release(sid, r["index"])
+        n_pipe = max(4, min(args.steps, 12))
+
+        def consume():
+            for _ in range(n_pipe):
+                r = svc.poll(sid, timeout_ms=60000)
+                svc.release(sid, r["index"])
+
+        barrier(pg, dev)
+        t0 = time.perf_counter()
+        th = threading.Thread(target=consume)
+        th.start()
+        for k in range(n_pipe):
+            svc.reserve(sid, timeout_ms=60000)
+            svc.commit(sid, R + k)
+        th.join()
+        dtp = max_over_ranks((time.perf_counter() - t0) / n_pipe, pg, dev)
+        svc.close()
+        e2e = {"value": world * step_cmac / dtp / 1e12, "unit": "cMAC TOPS",
                "h2d_bytes_per_step": int(x.nbytes), "d2h_bytes_per_step": int(h_out.numel() * 4),
-               "ms_per_step": dt * 1e3}
+               "ms_per_step": dtp * 1e3,
+               "api": "streaming service (xe_service_*): gulps in from pinned host memory, visibilities "
+                      "back to pinned host memory, consecutive gulps pipelined",
+               "sync": sync}
 
     peaks = measured_peaks()
     flops_per_launch = 8 * step_cmac  # 4 real multiplies + 4 adds per complex MAC
