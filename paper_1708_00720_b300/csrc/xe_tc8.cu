@@ -88,7 +88,8 @@ constexpr int kRawStage = 2 * kRawTile;         // I box, J box
 constexpr int kOpBytes = kOpStages * kOpStage;
 constexpr int kRawBytes = kRawStages * kRawStage;
 constexpr int kStageBytes = 4 * 32 * 32 * 8;    // per epilogue warp: 32 rows x 32 int2
-constexpr int kSumsBytes = 2 * 4 * kTile * 4 + 2 * kTile * 4;  // 2 slots x {P_I,Q_I,P_J,Q_J} + column corrections
+constexpr int kSumsBytes = 2 * 4 * kTile * 4 + 2 * kTile * 4 + kTile * 4;
+// 2 slots x {P_I,Q_I,P_J,Q_J}, column corrections, per-row triangle offsets
 constexpr int kBarOffset = kOpBytes + kRawBytes + kStageBytes + kSumsBytes;
 constexpr int kNumBars = 2 * kRawStages + 2 * kOpStages + 2 + 2 + 2 + 1;
 constexpr int kSmemBytes = kBarOffset + kNumBars * 8 + 16 + 1024;
@@ -107,6 +108,7 @@ struct Smem {
   int2* stage;     // [4 warps][32 rows][32], column index XOR row
   int* sums;       // [2][4][128]
   float* colcorr;  // [2][128]: per-column bias corrections of the current unit (re, im)
+  int* rowoff;     // [128]: packed-triangle offset i (i + 1) / 2 of each accumulator row's input i
   uint64_t *raw_full, *raw_empty, *op_full, *op_empty;
   uint64_t *acc_full, *acc_empty, *sums_full, *sums_empty, *final_bar;
   uint32_t* tmem_slot;
@@ -120,6 +122,7 @@ __device__ __forceinline__ Smem carve(uint8_t* base) {
   p.stage = reinterpret_cast<int2*>(base + kOpBytes + kRawBytes);
   p.sums = reinterpret_cast<int*>(base + kOpBytes + kRawBytes + kStageBytes);
   p.colcorr = reinterpret_cast<float*>(p.sums + 2 * 4 * kTile);
+  p.rowoff = reinterpret_cast<int*>(p.colcorr + 2 * kTile);
   uint64_t* b = reinterpret_cast<uint64_t*>(base + kBarOffset);
   p.raw_full = b; b += kRawStages;
   p.raw_empty = b; b += kRawStages;
@@ -546,6 +549,11 @@ xcorr_tc8_kernel(const __grid_constant__ CUtensorMap tmap, TcParams prm) {
         s.colcorr[L] = static_cast<float>(-8 * (PJ[L] + QJ[L]));
         s.colcorr[kTile + L] = static_cast<float>(-8 * (PJ[L] - QJ[L]));
       }
+      {
+        // this warp's 32 rows: packed-triangle row offsets (N <= 8192 fits int)
+        const int gi = bi * kTile + il;
+        s.rowoff[L] = gi < prm.N ? gi * (gi + 1) / 2 : 0;
+      }
       asm volatile("bar.sync 1, 128;" ::: "memory");
       if (ok && !wait_or_abort(s.acc_full, ui & 1, lim, abort_flag)) {
         fail(s, prm.err, kErrWaitAccFull);
@@ -583,17 +591,34 @@ xcorr_tc8_kernel(const __grid_constant__ CUtensorMap tmap, TcParams prm) {
           __syncwarp();
           // 32 rows x 32 baselines: each row is 256 contiguous bytes of the accumulator
           const int gj = bj * kTile + cc + lane;
+          const int* ro = s.rowoff + 32 * quad;
+          int2* accj = reinterpret_cast<int2*>(prm.acc) + chan_base + gj;
+          // a tile pair strictly below the diagonal and inside N needs no checks
+          const bool full = bi > bj && bi * kTile + kTile <= prm.N;
+          if (full && !prm.accumulate) {
 #pragma unroll 4
-          for (int r = 0; r < 32; ++r) {
-            const int gi = bi * kTile + lane_to_input(32 * quad + r);
-            if (gi < prm.N && gj <= gi && gj < prm.N) {
+            for (int r = 0; r < 32; ++r) accj[ro[r]] = stg[r * 32 + (lane ^ r)];
+          } else if (full) {
+#pragma unroll 4
+            for (int r = 0; r < 32; ++r) {
               const int2 v = stg[r * 32 + (lane ^ r)];
-              int2* dst = reinterpret_cast<int2*>(prm.acc) + chan_base + static_cast<long long>(gi) * (gi + 1) / 2 + gj;
-              if (prm.accumulate) {
-                const int2 o = *dst;
-                *dst = make_int2(o.x + v.x, o.y + v.y);
-              } else {
-                *dst = v;
+              int2* dst = accj + ro[r];
+              const int2 o = *dst;
+              *dst = make_int2(o.x + v.x, o.y + v.y);
+            }
+          } else {
+#pragma unroll 4
+            for (int r = 0; r < 32; ++r) {
+              const int gi = bi * kTile + lane_to_input(32 * quad + r);
+              if (gi < prm.N && gj <= gi && gj < prm.N) {
+                const int2 v = stg[r * 32 + (lane ^ r)];
+                int2* dst = accj + ro[r];
+                if (prm.accumulate) {
+                  const int2 o = *dst;
+                  *dst = make_int2(o.x + v.x, o.y + v.y);
+                } else {
+                  *dst = v;
+                }
               }
             }
           }

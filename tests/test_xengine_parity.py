@@ -245,3 +245,16 @@ def test_large_n_workload_sampled(xe, operand):
     v = run(xe, x, operand)
     properties_check(v, x)
     sampled_check(v, x, np.random.default_rng(2))
+
+
+@pytest.mark.parametrize("operand", OPS)
+def test_maximum_inputs_sampled(xe, operand):
+    """8192 inputs (the largest accepted), one channel, a ragged 200-sample
+    gulp: sampled baselines one by one against the oracle, plus the
+    properties that hold at any size."""
+    x = synth.uniform_bytes((200, 1, 8192), seed=12)
+    v = run(xe, x, operand)
+    properties_check(v, x)
+    sampled_check(v, x, np.random.default_rng(3))
+    for i, j in ((8191, 0), (8191, 8191), (4096, 4095), (128, 127), (8191, 8064)):
+        assert tuple(v[0, oracle.tri_index(i, j)]) == oracle.correlate_one(x, 0, i, j)
