@@ -73,11 +73,19 @@ constexpr int kOpStages = XE_TC8_OP_STAGES;
 // A warp that issues a TMA tile load is held for roughly 750 cycles per
 // instruction on this part, whatever the box size, so raw tiles move in 16 KB
 // boxes (one per stage) issued by two producer warps: warp 0 for I, warp 2 for J.
+// Warp roles.  Warp w issues from SM sub-partition w % 4; the A-side and
+// epilogue warps need one warp per TMEM lane quadrant (w % 4), and the MMA
+// warp's sub-partition (1) carries one B-side warp instead of two.
+//   0: TMA I tiles   1: MMA issuer   2: TMA J tiles   4-7: A side
+//   3, 8, 10-15: B side   9: idle   16-19: epilogue
 constexpr int kAWarp0 = 4;                // 4 A-side warps, one per TMEM lane quadrant
-constexpr int kBWarp0 = 8;                // 8 B-side warps
 constexpr int kBWarps = 8;
-constexpr int kEpiWarp0 = kBWarp0 + kBWarps;  // 4 epilogue warps, one per quadrant
+constexpr int kEpiWarp0 = 16;             // 4 epilogue warps, one per quadrant
 constexpr int kThreads = 32 * (kEpiWarp0 + 4);
+// B-side warp -> its index 0..7, -1 for other roles
+__device__ __forceinline__ int b_ordinal(int w) {
+  return w == 3 ? 0 : (w == 8 ? 1 : (w >= 10 && w < 16 ? w - 8 : -1));
+}
 constexpr int kStageArrivals = 4 + kBWarps;   // A and B warps, once per stage
 constexpr int kTmemCols = 512;
 constexpr int kTmemA0 = 256;              // A stages: 64 columns each (4 steps x (re 8 + im 8))
@@ -378,7 +386,7 @@ xcorr_tc8_kernel(const __grid_constant__ CUtensorMap tmap, TcParams prm) {
       mma_commit(s.final_bar);
       if (!mbar_wait(s.final_bar, 0, lim)) atomicOr(prm.err, kErrWaitFinal);
     }
-  } else if (warp >= kAWarp0 && warp < kBWarp0) {
+  } else if (warp >= kAWarp0 && warp < kAWarp0 + 4) {
     // ====================================================== A side -> TMEM
     const int quad = warp & 3;                 // TMEM lane quadrant of this warp
     const int pj = lane >> 2;                  // input pair of this lane within a chunk
@@ -386,6 +394,10 @@ xcorr_tc8_kernel(const __grid_constant__ CUtensorMap tmap, TcParams prm) {
     bool ok = true;
     for (int u = blockIdx.x; u < prm.units && ok; u += gridDim.x, ++ui) {
       int aP[2][2] = {{0, 0}, {0, 0}}, aQ[2][2] = {{0, 0}, {0, 0}};  // [chunk h][input 2p + e]
+      // byte-lane partial sums (8 samples <= 15 per add and stage step: <= 240
+      // per lane after two stages), folded into aP / aQ every second stage
+      uint32_t bP[2][2] = {{0u, 0u}, {0u, 0u}}, bQ[2][2] = {{0u, 0u}, {0u, 0u}};
+      int since_fold = 0;
       for (int ks = 0; ks < nks; ks += kSteps, ++sit) {
         const int rst = sit % kRawStages, ost = sit % kOpStages;
         if (!wait_or_abort(&s.raw_full[rst], (sit / kRawStages) & 1, lim, abort_flag)) {
@@ -411,10 +423,10 @@ xcorr_tc8_kernel(const __grid_constant__ CUtensorMap tmap, TcParams prm) {
             const uint32_t w2 = __byte_perm(d0, d1, 0x7531), w3 = __byte_perm(d2, d3, 0x7531);
             const uint32_t re0 = biased_re(w0), re1 = biased_re(w1), re2 = biased_re(w2), re3 = biased_re(w3);
             const uint32_t im0 = biased_im(w0), im1 = biased_im(w1), im2 = biased_im(w2), im3 = biased_im(w3);
-            aP[h][0] += byte_sum(re0 + re1);
-            aP[h][1] += byte_sum(re2 + re3);
-            aQ[h][0] += byte_sum(im0 + im1);
-            aQ[h][1] += byte_sum(im2 + im3);
+            bP[h][0] += re0 + re1;
+            bP[h][1] += re2 + re3;
+            bQ[h][0] += im0 + im1;
+            bQ[h][1] += im2 + im3;
             const uint32_t ta = ta0 + (static_cast<uint32_t>(32 * quad + 16 * h) << 16) + 16 * sub;
             tmem_st_16x256b_x2(ta, re0, re1, re2, re3, im0, im1, im2, im3);
           }
@@ -425,6 +437,17 @@ xcorr_tc8_kernel(const __grid_constant__ CUtensorMap tmap, TcParams prm) {
         if (lane == 0) {
           mbar_arrive(&s.op_full[ost]);
           mbar_arrive(&s.raw_empty[rst]);
+        }
+        if (++since_fold == 2 || ks + kSteps >= nks) {
+#pragma unroll
+          for (int h = 0; h < 2; ++h)
+#pragma unroll
+            for (int e = 0; e < 2; ++e) {
+              aP[h][e] += byte_sum(bP[h][e]);
+              aQ[h][e] += byte_sum(bQ[h][e]);
+              bP[h][e] = bQ[h][e] = 0u;
+            }
+          since_fold = 0;
         }
       }
       if (!ok) break;
@@ -457,9 +480,9 @@ xcorr_tc8_kernel(const __grid_constant__ CUtensorMap tmap, TcParams prm) {
       __syncwarp();
       if (lane == 0) mbar_arrive(&s.sums_full[slot]);
     }
-  } else if (warp >= kBWarp0 && warp < kEpiWarp0) {
+  } else if (b_ordinal(warp) >= 0) {
     // ====================================================== B side -> shared planes
-    const int ut = tid - kBWarp0 * 32;         // 0..255
+    const int ut = b_ordinal(warp) * 32 + lane;  // 0..255
     const int q = ut & 7, row = ut >> 3;       // 16-input chunk, time row within each step
     const uint32_t off = sw128(kappa(row), q); // K row kappa(row) of the B planes
     int sit = 0, ui = 0;
@@ -519,7 +542,7 @@ xcorr_tc8_kernel(const __grid_constant__ CUtensorMap tmap, TcParams prm) {
       __syncwarp();
       if (lane == 0) mbar_arrive(&s.sums_full[slot]);
     }
-  } else if (warp >= kEpiWarp0) {
+  } else if (warp >= kEpiWarp0 && warp < kEpiWarp0 + 4) {
     // ====================================================== epilogue
     // Never leaves the unit loop early (the named barriers below must be
     // reached equally often by all four warps); after an abort it only
