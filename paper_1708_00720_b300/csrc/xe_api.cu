@@ -162,7 +162,7 @@ xe_status enqueue_correlate(xe_plan* p, const uint8_t* d_gulp, int ntime, int ac
     prm.acc = p->d_acc;
     prm.err = p->d_err;
     prm.timeout_ns = kWaitTimeoutNs;
-    cudaError_t e = (eb == 1) ? xe::launch_xcorr_tc8(&map, prm, grid, stream)
+    cudaError_t e = (eb == 1) ? xe::launch_xcorr_tc8(&map, prm, p->num_sms, stream)
                               : xe::launch_xcorr_tc(eb, &map, prm, grid, stream);
     if (e != cudaSuccess) return cuda_fail(p, e, "tcgen05 launch");
     ++p->launches;

@@ -31,10 +31,11 @@ int tc_threads();
 cudaError_t launch_xcorr_tc(int eb, const CUtensorMap* tmap, const TcParams& prm, int grid,
                             cudaStream_t stream);
 
-// e4m3 X-engine with operand A in tensor memory (tmap: uint8 {N, C, T},
-// box {128, 1, 32}, 128-byte swizzle).
+// e4m3 X-engine on pairs of CTAs (tmap: uint8 {N, C, T}, box {128, 1, 128},
+// 128-byte swizzle).  prm.units is set here (channels x pair units); the grid
+// is at most max_ctas CTAs (an even number).
 int tc8_smem_bytes();
-cudaError_t launch_xcorr_tc8(const CUtensorMap* tmap, const TcParams& prm, int grid, cudaStream_t stream);
+cudaError_t launch_xcorr_tc8(const CUtensorMap* tmap, TcParams prm, int max_ctas, cudaStream_t stream);
 
 // Plain CUDA-core correlator (int8 dot products into int32), the baseline.
 cudaError_t launch_xcorr_cudacore(const uint8_t* gulp, int T, int C, int N, int32_t* acc,

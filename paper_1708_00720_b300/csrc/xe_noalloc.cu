@@ -127,8 +127,6 @@ extern "C" XE_API xe_status xe_correlate_noalloc(const uint8_t* d_gulp, int ntim
   if (!enc) return XE_ERR_CUDA;
   const size_t row_bytes = static_cast<size_t>(n_chan) * static_cast<size_t>(n_input);
   const int nt = (n_input + 127) / 128;
-  const long long units = static_cast<long long>(n_chan) * nt * (nt + 1) / 2;
-  const int grid = static_cast<int>(units < sms ? units : sms);
   for (int t0 = 0; t0 < ntime; t0 += kLaunchNtime) {
     const int T = (ntime - t0) < kLaunchNtime ? (ntime - t0) : kLaunchNtime;
     const uint8_t* slice = d_gulp + static_cast<size_t>(t0) * row_bytes;
@@ -146,13 +144,13 @@ extern "C" XE_API xe_status xe_correlate_noalloc(const uint8_t* d_gulp, int ntim
     prm.N = n_input;
     prm.C = n_chan;
     prm.nt = nt;
-    prm.units = static_cast<int>(units);
+    prm.units = 0;  // set by the launcher
     prm.nks = 4 * ((T + 127) / 128);
     prm.accumulate = t0 > 0 ? 1 : 0;  // the first launch overwrites the scratch accumulator
     prm.acc = d_acc;
     prm.err = d_err;
     prm.timeout_ns = kWaitTimeoutNs;
-    if (xe::launch_xcorr_tc8(&map, prm, grid, s) != cudaSuccess) return XE_ERR_CUDA;
+    if (xe::launch_xcorr_tc8(&map, prm, sms, s) != cudaSuccess) return XE_ERR_CUDA;
   }
   cudaError_t e = (out_type == XE_OUT_CI32)
                       ? cudaMemcpyAsync(d_vis, d_acc, out_bytes, cudaMemcpyDeviceToDevice, s)

@@ -1,4 +1,4 @@
-// tcgen05 X-engine, e4m3 operands, operand A fed from tensor memory.
+// tcgen05 X-engine, e4m3 operands: pairs of CTAs on one M = 256 MMA.
 //
 // Computes, like every X-engine path here (the linear-algebra module of the
 // paper's section "Back end" applied to the 4+4-bit samples of section
@@ -7,34 +7,48 @@
 // into an int32 accumulator [C][N(N+1)/2][2] (packed lower triangle).
 //
 // Why this layout.  On sm_103 the tensor core reads shared-memory operands
-// through the same data pipe as ld/st.shared.  A 128 x 128 x 32 e4m3 MMA with
-// both operands in shared memory needs about one pipe-width of bytes per
-// clock by itself, so every byte the unpack warps move through shared memory
-// steals tensor-core time.  Here the I tile (operand A) never touches the
-// shared-memory operand path: it is transposed in registers and written to
-// tensor memory with tcgen05.st; only the J tile (operand B) is staged in
-// shared memory.  Per 32-sample step of a 128 x 128 tile pair the pipe moves
-// ~32 KB instead of ~56 KB.
+// through the same data pipe as ld/st.shared, and the unpack warps compete
+// with the MMA issuer for issue slots.  Two measures cut that traffic:
+//  * operand A (the I tile) never touches shared memory: it is transposed in
+//    registers and written to tensor memory with tcgen05.st;
+//  * the two CTAs of a cluster run one tcgen05.mma.cta_group::2 per step:
+//    M = 256 rows (128 I inputs in each CTA's tensor memory), N = 128 J
+//    inputs of which each CTA holds 64 rows of operand B in its own shared
+//    memory.  Both CTAs share one J tile, so each unpacks and stores only
+//    half of it and its tensor core reads only half of B from local shared
+//    memory.  Each CTA's 128 x 128 accumulator lives in its own TMEM.
+// Per 32-sample step the pipe of one SM moves ~16 KB of operand B instead of
+// ~32 KB, and the B unpack per SM halves.
 //
-// Per step (32 samples) of a unit (channel c, 128-input tiles I >= J):
+// Work: a pair unit is (channel c, J tile, I tile of CTA 0, I tile of
+// CTA 1).  The lower-triangle tile pairs (I >= J) of a channel are grouped
+// by J column two at a time; the odd one out of a column, (nt-1, j), is
+// computed as its transpose (I = j, J = nt-1) next to the last diagonal tile
+// and written back conjugated and transposed.  If the count is still odd,
+// CTA 1 repeats its partner's tile and writes nothing.
+//
+// Per step (32 samples) of a unit:
 //  * TMA loads the raw 32 x 128-byte time x input tiles of I and J into
-//    shared memory with the 128-byte swizzle.
-//  * A side (one warp per TMEM lane quadrant): ldmatrix.x4.trans reads a
-//    32-time x 16-input block as 16-bit pairs, four byte permutes regroup it
-//    so that each 32-bit word holds four samples of one input, the nibbles
-//    are split into biased e4m3 bytes (u = v + 8, exactly u * 2^-9) and
-//    tcgen05.st.16x256b writes the re and im planes (K = 32 bytes per row).
-//    Input 16g + 2p goes to TMEM lane 16g + p and input 16g + 2p + 1 to lane
-//    16g + p + 8; the four samples of a word follow a fixed permutation of
-//    time within the step (kappa below).
-//  * B side: the J raw tile is split into biased re / im planes in shared
-//    memory (MN-major, 128-byte swizzle), time row t stored at K row
-//    kappa(t) so both operands agree on the order of K.
-//  * MMA (one thread): D_re += A_re B_re^T + A_im B_im^T,
-//                      D_im += A_im B_re^T - A_re B_im^T   (negate-B bit).
-//  * Epilogue: D (single buffer, 256 TMEM columns) is drained through a
-//    swizzled 128 KB shared staging buffer, the bias is removed exactly from
-//    per-input sums of u, and rows are written coalesced to the accumulator:
+//    shared memory with the 128-byte swizzle (J is skipped when I == J).
+//  * A side (two warps per TMEM lane quadrant, one per 16-input chunk):
+//    ldmatrix.x4.trans reads a 32-time x 16-input block as 16-bit pairs,
+//    four byte permutes regroup it so that each 32-bit word holds four
+//    samples of one input, the nibbles become biased e4m3 bytes
+//    (u = v + 8, exactly u * 2^-9) and tcgen05.st.16x256b writes the re and
+//    im planes.  Input 16g + 2p goes to row 16g + p and input 16g + 2p + 1 to
+//    row 16g + p + 8; the samples of a word follow a fixed permutation of
+//    time within the step, the same on both operands.
+//  * B side (four warps, one 16-input chunk of this CTA's half of J each):
+//    the same transposition, stored K-major with the 128-byte swizzle into
+//    shared memory (64 rows x 128 bytes per plane and stage), rows ordered
+//    like the A rows.
+//  * MMA (one thread of CTA 0): D_re += A_re B_re^T + A_im B_im^T,
+//                               D_im += A_im B_re^T - A_re B_im^T
+//    (negate-B bit); commits are multicast to both CTAs.
+//  * Epilogue (each CTA): D (single buffer, 256 TMEM columns) is read per
+//    32-column chunk, the bias is removed exactly from per-input sums of u
+//    (the column sums of the other half of J are read from the partner's
+//    shared memory) and rows are written coalesced to the accumulator:
 //      Re V = D_re - 8 (P_i + Q_i + P_j + Q_j) + 128 T'
 //      Im V = D_im + 8 (P_i - Q_i) - 8 (P_j - Q_j).
 // Exactness: all partial sums of D stay below 450 T' <= 2^24 for T' <= 37282;
@@ -53,56 +67,60 @@ namespace xe {
 namespace tc8 {
 
 constexpr int kTile = 128;
+constexpr int kHalf = 64;                 // J inputs whose B rows one CTA of the pair holds
 constexpr int kStep = 32;                 // samples per MMA step (K = 32 e4m3)
 constexpr int kSteps = 4;                 // steps per pipeline stage (128 samples)
 constexpr int kRawSub = kStep * kTile;    // 4096 bytes: one step of one raw tile
 constexpr int kRawTile = kSteps * kRawSub;  // 16 KB TMA box: 128 time rows x 128 inputs
-constexpr int kPlane = kStep * kTile;     // one e4m3 plane (re or im) of one tile, one step
 #ifndef XE_TC8_RAW_STAGES
-#define XE_TC8_RAW_STAGES 2
+#define XE_TC8_RAW_STAGES 3
 #endif
 #ifndef XE_TC8_OP_STAGES
-#define XE_TC8_OP_STAGES 3
+#define XE_TC8_OP_STAGES 4
 #endif
 // Synchronisation happens once per stage of 4 steps: the tensor core's
 // instruction queue holds only a few MMAs, so every barrier check or commit
-// between MMAs costs issue bubbles, and each warp's wait-wake latency is a
-// few hundred cycles.  Per stage the MMA thread issues 16 MMAs and one commit.
+// between MMAs costs issue bubbles.  Per stage the MMA thread issues 16 MMAs
+// and one commit.  A warp that issues a TMA tile load is held for roughly
+// 750 cycles per instruction, so raw tiles move in 16 KB boxes (one per
+// stage) issued by two producer warps.
 constexpr int kRawStages = XE_TC8_RAW_STAGES;
 constexpr int kOpStages = XE_TC8_OP_STAGES;
-// A warp that issues a TMA tile load is held for roughly 750 cycles per
-// instruction on this part, whatever the box size, so raw tiles move in 16 KB
-// boxes (one per stage) issued by two producer warps: warp 0 for I, warp 2 for J.
-// Warp roles.  Warp w issues from SM sub-partition w % 4; the A-side and
-// epilogue warps need one warp per TMEM lane quadrant (w % 4), and the MMA
-// warp's sub-partition (1) carries one B-side warp instead of two.
-//   0: TMA I tiles   1: MMA issuer   2: TMA J tiles   4-7: A side
-//   3, 8, 10-15: B side   9: idle   16-19: epilogue
-constexpr int kAWarp0 = 4;                // 4 A-side warps, one per TMEM lane quadrant
-constexpr int kBWarps = 8;
-constexpr int kEpiWarp0 = 16;             // 4 epilogue warps, one per quadrant
-constexpr int kThreads = 32 * (kEpiWarp0 + 4);
-// B-side warp -> its index 0..7, -1 for other roles
-__device__ __forceinline__ int b_ordinal(int w) {
-  return w == 3 ? 0 : (w == 8 ? 1 : (w >= 10 && w < 16 ? w - 8 : -1));
-}
-constexpr int kStageArrivals = 4 + kBWarps;   // A and B warps, once per stage
-constexpr int kTmemCols = 512;
-constexpr int kTmemA0 = 256;              // A stages: 64 columns each (4 steps x (re 8 + im 8))
-constexpr int kTmemAStage = 16 * kSteps;
-
-constexpr int kOpStage = kSteps * 2 * kPlane;   // B planes of 4 steps: [step][re, im][kPlane]
+constexpr int kPlane = kHalf * kSteps * kStep;  // 8 KB: 64 rows x 128 K bytes, K-major
+constexpr int kOpStage = 2 * kPlane;            // re plane, im plane
 constexpr int kRawStage = 2 * kRawTile;         // I box, J box
 constexpr int kOpBytes = kOpStages * kOpStage;
 constexpr int kRawBytes = kRawStages * kRawStage;
 constexpr int kStageBytes = 4 * 32 * 32 * 8;    // per epilogue warp: 32 rows x 32 int2
-constexpr int kSumsBytes = 2 * 4 * kTile * 4 + 2 * kTile * 4 + kTile * 4;
-// 2 slots x {P_I,Q_I,P_J,Q_J}, column corrections, per-row triangle offsets
+constexpr int kSlotInts = 2 * kTile + 2 * kHalf;  // P_I, Q_I (128 each), P_J, Q_J of this CTA's half
+constexpr int kSumsBytes = 2 * kSlotInts * 4 + 2 * kTile * 4 + 2 * kTile * 4;
+// 2 slots of sums, column corrections (re, im), row and column triangle offsets
 constexpr int kBarOffset = kOpBytes + kRawBytes + kStageBytes + kSumsBytes;
 constexpr int kNumBars = 2 * kRawStages + 2 * kOpStages + 2 + 2 + 2 + 1;
 constexpr int kSmemBytes = kBarOffset + kNumBars * 8 + 16 + 1024;
 static_assert(kSmemBytes <= 227 * 1024, "shared memory budget");
+static_assert(kOpBytes % 1024 == 0 && kRawBytes % 1024 == 0, "swizzled tiles need 1024-byte alignment");
+
+// Warp roles.  Warp w issues from SM sub-partition w % 4; the A-side and
+// epilogue warps need their warp index = TMEM lane quadrant (mod 4).
+//   0: TMA I tiles   1: MMA issuer (CTA 0)   2: TMA J tiles
+//   4-7, 12-15: A side (quadrant w % 4, chunk (w >> 3) & 1)
+//   3, 8, 10, 11: B side (chunk 0..3 of this CTA's half of J)   9: idle
+//   16-19: epilogue
+constexpr int kEpiWarp0 = 16;
+constexpr int kThreads = 32 * (kEpiWarp0 + 4);
+constexpr int kAWarps = 8;
+constexpr int kBWarps = 4;
+constexpr int kStageArrivals = kAWarps + kBWarps;   // per CTA and stage
+constexpr int kTmemCols = 512;
+constexpr int kTmemA0 = 256;              // A stages: 64 columns each (4 steps x (re 8 + im 8))
+constexpr int kTmemAStage = 16 * kSteps;
 static_assert(kTmemA0 + kTmemAStage * kOpStages <= kTmemCols, "tensor memory budget");
+
+__device__ __forceinline__ bool is_a_warp(int w) { return (w >= 4 && w < 8) || (w >= 12 && w < 16); }
+__device__ __forceinline__ int b_ordinal(int w) {
+  return w == 3 ? 0 : (w == 8 ? 1 : (w == 10 ? 2 : (w == 11 ? 3 : -1)));
+}
 
 enum ErrCode : int {
   kErrWaitRawFull = 1 << 0, kErrWaitRawEmpty = 1 << 1, kErrWaitOpFull = 1 << 2,
@@ -111,12 +129,13 @@ enum ErrCode : int {
 };
 
 struct Smem {
-  uint8_t* op;     // [kOpStages][kSteps][2][kPlane]  B planes
+  uint8_t* op;     // [kOpStages][re, im][64 rows x 128 K bytes]  B planes (this CTA's half)
   uint8_t* raw;    // [kRawStages][2][kRawTile]
   int2* stage;     // [4 warps][32 rows][32], column index XOR row
-  int* sums;       // [2][4][128]
+  int* sums;       // [2][kSlotInts]
   float* colcorr;  // [2][128]: per-column bias corrections of the current unit (re, im)
   int* rowoff;     // [128]: packed-triangle offset i (i + 1) / 2 of each accumulator row's input i
+  int* coloff;     // [128]: the same for each accumulator column's input j
   uint64_t *raw_full, *raw_empty, *op_full, *op_empty;
   uint64_t *acc_full, *acc_empty, *sums_full, *sums_empty, *final_bar;
   uint32_t* tmem_slot;
@@ -129,8 +148,9 @@ __device__ __forceinline__ Smem carve(uint8_t* base) {
   p.raw = base + kOpBytes;
   p.stage = reinterpret_cast<int2*>(base + kOpBytes + kRawBytes);
   p.sums = reinterpret_cast<int*>(base + kOpBytes + kRawBytes + kStageBytes);
-  p.colcorr = reinterpret_cast<float*>(p.sums + 2 * 4 * kTile);
+  p.colcorr = reinterpret_cast<float*>(p.sums + 2 * kSlotInts);
   p.rowoff = reinterpret_cast<int*>(p.colcorr + 2 * kTile);
+  p.coloff = p.rowoff + kTile;
   uint64_t* b = reinterpret_cast<uint64_t*>(base + kBarOffset);
   p.raw_full = b; b += kRawStages;
   p.raw_empty = b; b += kRawStages;
@@ -146,13 +166,54 @@ __device__ __forceinline__ Smem carve(uint8_t* base) {
   return p;
 }
 
+// ------------------------------------------------------------ cluster helpers
+__device__ __forceinline__ uint32_t cluster_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ void cluster_sync() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+// Shared::cluster address of the same object in CTA `cta` of this cluster.
+__device__ __forceinline__ uint32_t peer_addr(const void* p, uint32_t cta) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(smem_u32(p)), "r"(cta));
+  return r;
+}
+// Arrive (release, cluster scope) on the barrier at this offset in CTA `cta`.
+__device__ __forceinline__ void arrive_at(uint64_t* bar, uint32_t cta) {
+  asm volatile("mbarrier.arrive.release.cluster.shared::cluster.b64 _, [%0];" ::"r"(peer_addr(bar, cta))
+               : "memory");
+}
+// Arrive without release semantics: for signals that publish no memory
+// writes (the arriving thread only finished reading), so the arrival does not
+// wait for the thread's outstanding global stores.
+__device__ __forceinline__ void arrive_relaxed_at(uint64_t* bar, uint32_t cta) {
+  asm volatile("mbarrier.arrive.relaxed.cluster.shared::cluster.b64 _, [%0];" ::"r"(peer_addr(bar, cta))
+               : "memory");
+}
+__device__ __forceinline__ int ld_peer(const int* p, uint32_t cta) {
+  int v;
+  asm volatile("ld.shared::cluster.u32 %0, [%1];" : "=r"(v) : "r"(peer_addr(p, cta)) : "memory");
+  return v;
+}
+// One test of the phase with cluster-scope acquire (arrivals may come from
+// the partner CTA), parked by the hardware up to the suspend hint.
+__device__ __forceinline__ bool try_wait_c(uint32_t bar_addr, uint32_t parity) {
+  uint32_t ok;
+  asm volatile("{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.acquire.cluster.shared::cta.b64 p, [%1], %2, %3;\n\t"
+               "selp.u32 %0, 1, 0, p;\n\t}"
+               : "=r"(ok) : "r"(bar_addr), "r"(parity), "r"(0x989680u) : "memory");
+  return ok != 0;
+}
 __device__ __forceinline__ bool wait_or_abort(uint64_t* bar, uint32_t parity, uint64_t limit_ns,
                                               volatile int* abort_flag) {
   const uint32_t a = smem_u32(bar);
-  if (mbar_try_wait(a, parity)) return true;
+  if (try_wait_c(a, parity)) return true;
   const uint64_t t0 = global_timer_ns();
   while (true) {
-    if (mbar_try_wait(a, parity)) return true;
+    if (try_wait_c(a, parity)) return true;
     if (*abort_flag) return false;
     if (global_timer_ns() - t0 > limit_ns) return false;
   }
@@ -163,33 +224,85 @@ __device__ __forceinline__ void fail(const Smem& s, int* err, int code) {
   atomicOr(err, code);
 }
 
-__device__ __forceinline__ void decode_unit(int u, int npairs, int& c, int& bi, int& bj) {
-  c = u / npairs;
-  const int p = u - c * npairs;
-  int i = static_cast<int>((sqrtf(8.0f * p + 1.0f) - 1.0f) * 0.5f);
-  while ((i + 1) * (i + 2) / 2 <= p) ++i;
-  while (i * (i + 1) / 2 > p) --i;
-  bi = i;
-  bj = p - i * (i + 1) / 2;
+// ----------------------------------------------------------- tcgen05 (pair)
+__device__ __forceinline__ void mma2_f8_tmem_a(uint32_t d_tmem, uint32_t a_tmem, uint64_t b_desc,
+                                               uint32_t idesc, uint32_t accumulate) {
+  asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+               "tcgen05.mma.cta_group::2.kind::f8f6f4 [%0], [%1], %2, %3, p;\n\t}"
+               ::"r"(d_tmem), "r"(a_tmem), "l"(b_desc), "r"(idesc), "r"(accumulate));
+}
+// Completion of this thread's earlier MMAs arrives on `bar` in both CTAs.
+__device__ __forceinline__ void commit2(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;"
+               ::"r"(smem_u32(bar)), "h"(static_cast<uint16_t>(3)) : "memory");
+}
+// K-major operand, 128-byte swizzle: 8-row groups 1024 B apart.
+__device__ __forceinline__ uint64_t sdesc_k_sw128(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= static_cast<uint64_t>((saddr >> 4) & 0x3FFFu);
+  d |= 1ull << 16;                                     // leading byte offset: unused when swizzled
+  d |= static_cast<uint64_t>(1024 >> 4) << 32;         // stride byte offset
+  d |= 1ull << 46;                                     // descriptor version for tcgen05
+  d |= 2ull << 61;                                     // SWIZZLE_128B
+  return d;
 }
 
-__device__ __forceinline__ uint4 lds128(const void* p) {
-  uint4 v;
-  asm volatile("ld.shared.v4.u32 {%0,%1,%2,%3}, [%4];"
-               : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "r"(smem_u32(p)) : "memory");
-  return v;
+// -------------------------------------------------------------- work units
+// Pair units per channel for nt tiles per side (see the file comment).
+__host__ __device__ inline int pairs_per_channel(int nt) {
+  int p = 0;
+  for (int j = 0; j < nt - 1; ++j) p += (nt - j) >> 1;
+  const int e = 1 + (nt - 1) / 2;  // last column: diagonal tile + transposed odd ones out
+  return p + (e + 1) / 2;
 }
-__device__ __forceinline__ void sts128(void* p, uint4 v) {
-  asm volatile("st.shared.v4.u32 [%0], {%1,%2,%3,%4};"
-               ::"r"(smem_u32(p)), "r"(v.x), "r"(v.y), "r"(v.z), "r"(v.w) : "memory");
+
+struct Unit {
+  int c, ti, tj;   // channel, this CTA's I tile, the pair's J tile
+  bool transposed; // computed block is the transpose of the lower-triangle tile (tj, ti)
+  bool write;      // false: duplicate of the partner's tile, kept off the output
+};
+
+__device__ __forceinline__ Unit decode_unit(int u, int per_chan, int nt, int rank) {
+  Unit t;
+  t.c = u / per_chan;
+  int e = u - t.c * per_chan;
+  t.transposed = false;
+  t.write = true;
+  for (int j = 0; j < nt - 1; ++j) {
+    const int np = (nt - j) >> 1;
+    if (e < np) {
+      t.ti = j + 2 * e + rank;
+      t.tj = j;
+      return t;
+    }
+    e -= np;
+  }
+  const int ne = 1 + (nt - 1) / 2;
+  int k = 2 * e + rank;
+  if (k >= ne) {  // odd count: repeat the partner's tile
+    k = 2 * e;
+    t.write = false;
+  }
+  t.tj = nt - 1;
+  if (k == 0) {
+    t.ti = nt - 1;
+  } else {  // odd one out of column j = ((nt-1) & 1) + 2 (k-1), i.e. tile (nt-1, j)
+    t.ti = ((nt - 1) & 1) + 2 * (k - 1);
+    t.transposed = true;
+  }
+  return t;
 }
+
+// ------------------------------------------------------------------ unpack
 __device__ __forceinline__ void ldsm_x4_trans(uint32_t addr, uint32_t& d0, uint32_t& d1, uint32_t& d2,
                                               uint32_t& d3) {
   asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];"
                : "=r"(d0), "=r"(d1), "=r"(d2), "=r"(d3) : "r"(addr) : "memory");
 }
-// .x2: the re plane (8 columns) and the im plane (the next 8) of one step in
-// one instruction
+__device__ __forceinline__ void sts64(uint32_t addr, uint32_t a, uint32_t b) {
+  asm volatile("st.shared.v2.u32 [%0], {%1,%2};" ::"r"(addr), "r"(a), "r"(b) : "memory");
+}
+// .x2: the re plane (8 columns) and the im plane (the next 8) of one step
 __device__ __forceinline__ void tmem_st_16x256b_x2(uint32_t taddr, uint32_t r0, uint32_t r1, uint32_t r2,
                                                    uint32_t r3, uint32_t r4, uint32_t r5, uint32_t r6,
                                                    uint32_t r7) {
@@ -200,80 +313,85 @@ __device__ __forceinline__ void tmem_st_16x256b_x2(uint32_t taddr, uint32_t r0, 
 __device__ __forceinline__ void tmem_st_wait() {
   asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
 }
-__device__ __forceinline__ void mma_f8_tmem_a(uint32_t d_tmem, uint32_t a_tmem, uint64_t b_desc,
-                                              uint32_t idesc, uint32_t accumulate) {
-  asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-               "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], [%1], %2, %3, p;\n\t}"
-               ::"r"(d_tmem), "r"(a_tmem), "l"(b_desc), "r"(idesc), "r"(accumulate));
-}
 
 __device__ __forceinline__ uint32_t biased_re(uint32_t w) { return ((w >> 4) & 0x0F0F0F0Fu) ^ 0x08080808u; }
 __device__ __forceinline__ uint32_t biased_im(uint32_t w) { return (w & 0x0F0F0F0Fu) ^ 0x08080808u; }
 __device__ __forceinline__ int byte_sum(uint32_t w) { return static_cast<int>(__dp4a(w, 0x01010101u, 0u)); }
-
-// K row of time sample t within a 32-sample step (the order the A-side
-// register transpose produces): t = 8a + 2j + b  ->  8j + 2a + b.
-__device__ __forceinline__ int kappa(int t) { return 8 * ((t & 7) >> 1) + 2 * (t >> 3) + (t & 1); }
 
 // Byte offset of 16-byte chunk q of row k in a 128-byte-swizzled tile.
 __device__ __forceinline__ uint32_t sw128(int k, int q) {
   return static_cast<uint32_t>(k * 128 + ((q ^ (k & 7)) << 4));
 }
 
-// Accumulator row (TMEM lane) -> input offset inside the I tile.
+// Accumulator row / column -> input offset inside its 128-input tile.
 __device__ __forceinline__ int lane_to_input(int L) {
   const int r = L & 15;
   return (L & ~15) + (r < 8 ? 2 * r : 2 * (r - 8) + 1);
 }
 
-// Per-thread sums of the biased J-side parts of 16 inputs (byte lanes,
-// flushed into 16-bit lanes before they can overflow).
-struct BSums {
-  uint32_t b_re[4], b_im[4], h_re[8], h_im[8];
+// One 32-time x 16-input block of a raw tile -> biased e4m3 words of the two
+// inputs 2p, 2p+1 (p = lane / 4): re0, re1 / im0, im1 hold 8 samples of
+// input 2p, re2, re3 / im2, im3 those of input 2p+1 (K bytes 8 (lane % 4)
+// to 8 (lane % 4) + 7 of the step).  Byte-lane sums go to bP / bQ.
+struct Words {
+  uint32_t re0, re1, re2, re3, im0, im1, im2, im3;
+};
+__device__ __forceinline__ Words unpack_block(uint32_t addr, uint32_t (&bP)[2], uint32_t (&bQ)[2]) {
+  uint32_t d0, d1, d2, d3;
+  ldsm_x4_trans(addr, d0, d1, d2, d3);
+  const uint32_t w0 = __byte_perm(d0, d1, 0x6420), w1 = __byte_perm(d2, d3, 0x6420);
+  const uint32_t w2 = __byte_perm(d0, d1, 0x7531), w3 = __byte_perm(d2, d3, 0x7531);
+  Words o;
+  o.re0 = biased_re(w0); o.re1 = biased_re(w1); o.re2 = biased_re(w2); o.re3 = biased_re(w3);
+  o.im0 = biased_im(w0); o.im1 = biased_im(w1); o.im2 = biased_im(w2); o.im3 = biased_im(w3);
+  bP[0] += o.re0 + o.re1;
+  bP[1] += o.re2 + o.re3;
+  bQ[0] += o.im0 + o.im1;
+  bQ[1] += o.im2 + o.im3;
+  return o;
+}
+
+// Per-lane sums of the biased parts of inputs 2p + e: byte lanes (at most
+// 4 x 30 per stage) folded into ints every second stage.
+struct PairSums {
+  uint32_t bP[2], bQ[2];
+  int P[2], Q[2];
   __device__ __forceinline__ void zero() {
-#pragma unroll
-    for (int k = 0; k < 4; ++k) b_re[k] = b_im[k] = 0u;
-#pragma unroll
-    for (int k = 0; k < 8; ++k) h_re[k] = h_im[k] = 0u;
+    bP[0] = bP[1] = bQ[0] = bQ[1] = 0u;
+    P[0] = P[1] = Q[0] = Q[1] = 0;
   }
-  __device__ __forceinline__ void add(const uint4& re, const uint4& im) {
-    b_re[0] += re.x; b_re[1] += re.y; b_re[2] += re.z; b_re[3] += re.w;
-    b_im[0] += im.x; b_im[1] += im.y; b_im[2] += im.z; b_im[3] += im.w;
-  }
-  __device__ __forceinline__ void flush() {
+  __device__ __forceinline__ void fold() {
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      h_re[2 * k] += b_re[k] & 0x00FF00FFu;
-      h_re[2 * k + 1] += (b_re[k] >> 8) & 0x00FF00FFu;
-      h_im[2 * k] += b_im[k] & 0x00FF00FFu;
-      h_im[2 * k + 1] += (b_im[k] >> 8) & 0x00FF00FFu;
-      b_re[k] = b_im[k] = 0u;
+    for (int e = 0; e < 2; ++e) {
+      P[e] += byte_sum(bP[e]);
+      Q[e] += byte_sum(bQ[e]);
+      bP[e] = bQ[e] = 0u;
     }
   }
-  __device__ __forceinline__ void publish(int* P, int* Q, int q) {
+  // the four lanes sharing an input pair hold disjoint samples
+  __device__ __forceinline__ void reduce() {
 #pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      const int i0 = 16 * q + 4 * k;
-      atomicAdd(&P[i0 + 0], static_cast<int>(h_re[2 * k] & 0xFFFFu));
-      atomicAdd(&P[i0 + 2], static_cast<int>(h_re[2 * k] >> 16));
-      atomicAdd(&P[i0 + 1], static_cast<int>(h_re[2 * k + 1] & 0xFFFFu));
-      atomicAdd(&P[i0 + 3], static_cast<int>(h_re[2 * k + 1] >> 16));
-      atomicAdd(&Q[i0 + 0], static_cast<int>(h_im[2 * k] & 0xFFFFu));
-      atomicAdd(&Q[i0 + 2], static_cast<int>(h_im[2 * k] >> 16));
-      atomicAdd(&Q[i0 + 1], static_cast<int>(h_im[2 * k + 1] & 0xFFFFu));
-      atomicAdd(&Q[i0 + 3], static_cast<int>(h_im[2 * k + 1] >> 16));
+    for (int e = 0; e < 2; ++e) {
+      P[e] += __shfl_xor_sync(0xFFFFFFFFu, P[e], 1);
+      P[e] += __shfl_xor_sync(0xFFFFFFFFu, P[e], 2);
+      Q[e] += __shfl_xor_sync(0xFFFFFFFFu, Q[e], 1);
+      Q[e] += __shfl_xor_sync(0xFFFFFFFFu, Q[e], 2);
     }
   }
 };
 
-__global__ void __launch_bounds__(kThreads, 1)
+__global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
 xcorr_tc8_kernel(const __grid_constant__ CUtensorMap tmap, TcParams prm) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                              ~static_cast<uintptr_t>(1023));
   const Smem s = carve(base);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int npairs = prm.nt * (prm.nt + 1) / 2;
+  const uint32_t rank = cluster_rank();
+  const uint32_t peer = rank ^ 1u;
+  const int cl = blockIdx.x >> 1, ncl = gridDim.x >> 1;
+  const int nt = prm.nt;
+  const int per_chan = pairs_per_channel(nt);
   const int nks = prm.nks;
   const uint64_t lim = prm.timeout_ns;
   volatile int* abort_flag = s.abort_flag;
@@ -284,27 +402,30 @@ xcorr_tc8_kernel(const __grid_constant__ CUtensorMap tmap, TcParams prm) {
       mbar_init(&s.raw_empty[k], kStageArrivals);
     }
     for (int k = 0; k < kOpStages; ++k) {
-      mbar_init(&s.op_full[k], kStageArrivals);
+      // own producers; in CTA 0 also the forwarded completion of CTA 1's stage
+      mbar_init(&s.op_full[k], kStageArrivals + (rank == 0 ? 1 : 0));
       mbar_init(&s.op_empty[k], 1);
     }
     mbar_init(s.acc_full, 1);
-    mbar_init(s.acc_empty, 4);
+    mbar_init(s.acc_empty, 8);       // both CTAs' epilogue warps (used in CTA 0)
     for (int k = 0; k < 2; ++k) {
-      mbar_init(&s.sums_full[k], kStageArrivals);
-      mbar_init(&s.sums_empty[k], 4);
+      mbar_init(&s.sums_full[k], kAWarps + 2 * kBWarps);  // own A and B warps, partner's B warps
+      mbar_init(&s.sums_empty[k], 8);                     // own and partner's epilogue warps
     }
     mbar_init(s.final_bar, 1);
     *s.abort_flag = 0;
     mbar_fence_init();
     tma_prefetch_desc(&tmap);
   }
-  for (int k = tid; k < 2 * 4 * kTile; k += kThreads) s.sums[k] = 0;
   if (warp == 0) {
-    tmem_alloc<kTmemCols>(s.tmem_slot);
-    tmem_relinquish();
+    // one warp of each CTA of the pair allocates together: same columns in both
+    asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;"
+                 ::"r"(smem_u32(s.tmem_slot)), "n"(kTmemCols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::2.sync.aligned;");
   }
   tc_fence_before();
   __syncthreads();
+  cluster_sync();   // both CTAs' barriers and tensor memory exist before any remote access
   tc_fence_after();
   const uint32_t tmem = *s.tmem_slot;
 
@@ -314,10 +435,9 @@ xcorr_tc8_kernel(const __grid_constant__ CUtensorMap tmap, TcParams prm) {
       const int tile = warp >> 1;               // 0: I tiles, 1: J tiles
       int rit = 0;                              // raw stage counter (4 steps each)
       bool ok = true;
-      for (int u = blockIdx.x; u < prm.units && ok; u += gridDim.x) {
-        int c, bi, bj;
-        decode_unit(u, npairs, c, bi, bj);
-        const bool diag = (bi == bj);
+      for (int u = cl; u < prm.units && ok; u += ncl) {
+        const Unit t = decode_unit(u, per_chan, nt, rank);
+        const bool own_diag = (t.ti == t.tj);
         for (int ks = 0; ks < nks; ks += kSteps, ++rit) {
           const int st = rit % kRawStages;
           if (!wait_or_abort(&s.raw_empty[st], ((rit / kRawStages) & 1) ^ 1, lim, abort_flag)) {
@@ -328,12 +448,12 @@ xcorr_tc8_kernel(const __grid_constant__ CUtensorMap tmap, TcParams prm) {
           uint8_t* dst = s.raw + st * kRawStage + tile * kRawTile;
           if (tile == 0) {
             mbar_arrive_expect_tx(&s.raw_full[st], kRawTile);
-            tma_load_3d(dst, &tmap, &s.raw_full[st], bi * kTile, c, ks * kStep);
-          } else if (!diag) {
+            tma_load_3d(dst, &tmap, &s.raw_full[st], t.ti * kTile, t.c, ks * kStep);
+          } else if (!own_diag) {
             mbar_arrive_expect_tx(&s.raw_full[st], kRawTile);
-            tma_load_3d(dst, &tmap, &s.raw_full[st], bj * kTile, c, ks * kStep);
+            tma_load_3d(dst, &tmap, &s.raw_full[st], t.tj * kTile, t.c, ks * kStep);
           } else {
-            mbar_arrive(&s.raw_full[st]);    // diagonal unit: the I tile serves both operands
+            mbar_arrive(&s.raw_full[st]);    // the I tile serves as J
           }
         }
       }
@@ -341,16 +461,36 @@ xcorr_tc8_kernel(const __grid_constant__ CUtensorMap tmap, TcParams prm) {
       for (int k = rit - 1; k >= 0 && k > rit - 1 - kRawStages; --k)
         mbar_wait(&s.raw_full[k % kRawStages], (k / kRawStages) & 1, lim);
     }
+  } else if (warp == 1 && rank == 1) {
+    // ====================================================== stage forwarder (CTA 1)
+    // A release at cluster scope costs the arriving thread several hundred
+    // cycles, so CTA 1's producers arrive on their local barrier and this
+    // thread alone tells CTA 0 that CTA 1's half of a stage is ready.
+    if (lane == 0) {
+      int sit = 0;
+      bool ok = true;
+      for (int u = cl; u < prm.units && ok; u += ncl) {
+        for (int ks = 0; ks < nks; ks += kSteps, ++sit) {
+          const int st = sit % kOpStages;
+          if (!wait_or_abort(&s.op_full[st], (sit / kOpStages) & 1, lim, abort_flag)) {
+            fail(s, prm.err, kErrWaitOpFull);
+            ok = false;
+            break;
+          }
+          arrive_at(&s.op_full[st], 0);
+        }
+      }
+    }
   } else if (warp == 1) {
-    // ====================================================== MMA issuer
+    // ====================================================== MMA issuer (CTA 0)
     if (lane == 0) {
       int sit = 0, ui = 0;
       bool ok = true;
-      // A from tensor memory (K-major), B MN-major; e4m3 x e4m3 -> f32, M = N = 128
-      constexpr uint32_t id_pos = (1u << 4) | (1u << 16) | ((128u >> 3) << 17) | ((128u >> 4) << 24);
+      // A from tensor memory, B K-major; e4m3 x e4m3 -> f32, M = 256 (pair), N = 128
+      constexpr uint32_t id_pos = (1u << 4) | ((128u >> 3) << 17) | ((256u >> 4) << 24);
       constexpr uint32_t id_neg = id_pos | (1u << 14);
       const uint32_t d_re = tmem, d_im = tmem + 128;
-      for (int u = blockIdx.x; u < prm.units && ok; u += gridDim.x, ++ui) {
+      for (int u = cl; u < prm.units && ok; u += ncl, ++ui) {
         if (!wait_or_abort(s.acc_empty, (ui & 1) ^ 1, lim, abort_flag)) {
           fail(s, prm.err, kErrWaitAccEmpty);
           break;
@@ -369,34 +509,33 @@ xcorr_tc8_kernel(const __grid_constant__ CUtensorMap tmap, TcParams prm) {
 #pragma unroll
           for (int sub = 0; sub < kSteps; ++sub) {
             const uint32_t a_re = a0 + 16 * sub, a_im = a_re + 8;
-            const uint32_t b = op + sub * 2 * kPlane;
-            const uint64_t b_re = sdesc_mn_sw128(b, 4096, 1024);
-            const uint64_t b_im = sdesc_mn_sw128(b + kPlane, 4096, 1024);
+            const uint64_t b_re = sdesc_k_sw128(op + 32 * sub);
+            const uint64_t b_im = sdesc_k_sw128(op + kPlane + 32 * sub);
             const uint32_t acc0 = (ks + sub) > 0 ? 1u : 0u;
-            mma_f8_tmem_a(d_re, a_re, b_re, id_pos, acc0);
-            mma_f8_tmem_a(d_re, a_im, b_im, id_pos, 1u);
-            mma_f8_tmem_a(d_im, a_im, b_re, id_pos, acc0);
-            mma_f8_tmem_a(d_im, a_re, b_im, id_neg, 1u);
+            mma2_f8_tmem_a(d_re, a_re, b_re, id_pos, acc0);
+            mma2_f8_tmem_a(d_re, a_im, b_im, id_pos, 1u);
+            mma2_f8_tmem_a(d_im, a_im, b_re, id_pos, acc0);
+            mma2_f8_tmem_a(d_im, a_re, b_im, id_neg, 1u);
           }
-          mma_commit(&s.op_empty[st]);
+          commit2(&s.op_empty[st]);
         }
         if (!ok) break;
-        mma_commit(s.acc_full);
+        commit2(s.acc_full);
       }
-      mma_commit(s.final_bar);
-      if (!mbar_wait(s.final_bar, 0, lim)) atomicOr(prm.err, kErrWaitFinal);
+      commit2(s.final_bar);
     }
-  } else if (warp >= kAWarp0 && warp < kAWarp0 + 4) {
+  } else if (is_a_warp(warp)) {
     // ====================================================== A side -> TMEM
     const int quad = warp & 3;                 // TMEM lane quadrant of this warp
-    const int pj = lane >> 2;                  // input pair of this lane within a chunk
+    const int h = (warp >> 3) & 1;             // which 16-input chunk of the quadrant
+    const int ch = 2 * quad + h;
+    const int pj = lane >> 2;                  // input pair of this lane within the chunk
+    const uint32_t lane_off = static_cast<uint32_t>(32 * quad + 16 * h) << 16;
     int sit = 0, ui = 0;
     bool ok = true;
-    for (int u = blockIdx.x; u < prm.units && ok; u += gridDim.x, ++ui) {
-      int aP[2][2] = {{0, 0}, {0, 0}}, aQ[2][2] = {{0, 0}, {0, 0}};  // [chunk h][input 2p + e]
-      // byte-lane partial sums (8 samples <= 15 per add and stage step: <= 240
-      // per lane after two stages), folded into aP / aQ every second stage
-      uint32_t bP[2][2] = {{0u, 0u}, {0u, 0u}}, bQ[2][2] = {{0u, 0u}, {0u, 0u}};
+    for (int u = cl; u < prm.units && ok; u += ncl, ++ui) {
+      PairSums ps;
+      ps.zero();
       int since_fold = 0;
       for (int ks = 0; ks < nks; ks += kSteps, ++sit) {
         const int rst = sit % kRawStages, ost = sit % kOpStages;
@@ -411,25 +550,11 @@ xcorr_tc8_kernel(const __grid_constant__ CUtensorMap tmap, TcParams prm) {
           break;
         }
         const uint32_t rawI_s = smem_u32(s.raw + rst * kRawStage);
-        const uint32_t ta0 = tmem + kTmemA0 + kTmemAStage * ost;
+        const uint32_t ta0 = tmem + kTmemA0 + kTmemAStage * ost + lane_off;
 #pragma unroll
         for (int sub = 0; sub < kSteps; ++sub) {
-#pragma unroll
-          for (int h = 0; h < 2; ++h) {
-            const int ch = 2 * quad + h;
-            uint32_t d0, d1, d2, d3;
-            ldsm_x4_trans(rawI_s + sub * kRawSub + sw128(lane, ch), d0, d1, d2, d3);
-            const uint32_t w0 = __byte_perm(d0, d1, 0x6420), w1 = __byte_perm(d2, d3, 0x6420);
-            const uint32_t w2 = __byte_perm(d0, d1, 0x7531), w3 = __byte_perm(d2, d3, 0x7531);
-            const uint32_t re0 = biased_re(w0), re1 = biased_re(w1), re2 = biased_re(w2), re3 = biased_re(w3);
-            const uint32_t im0 = biased_im(w0), im1 = biased_im(w1), im2 = biased_im(w2), im3 = biased_im(w3);
-            bP[h][0] += re0 + re1;
-            bP[h][1] += re2 + re3;
-            bQ[h][0] += im0 + im1;
-            bQ[h][1] += im2 + im3;
-            const uint32_t ta = ta0 + (static_cast<uint32_t>(32 * quad + 16 * h) << 16) + 16 * sub;
-            tmem_st_16x256b_x2(ta, re0, re1, re2, re3, im0, im1, im2, im3);
-          }
+          const Words w = unpack_block(rawI_s + sub * kRawSub + sw128(lane, ch), ps.bP, ps.bQ);
+          tmem_st_16x256b_x2(ta0 + 16 * sub, w.re0, w.re1, w.re2, w.re3, w.im0, w.im1, w.im2, w.im3);
         }
         tmem_st_wait();
         tc_fence_before();
@@ -439,61 +564,44 @@ xcorr_tc8_kernel(const __grid_constant__ CUtensorMap tmap, TcParams prm) {
           mbar_arrive(&s.raw_empty[rst]);
         }
         if (++since_fold == 2 || ks + kSteps >= nks) {
-#pragma unroll
-          for (int h = 0; h < 2; ++h)
-#pragma unroll
-            for (int e = 0; e < 2; ++e) {
-              aP[h][e] += byte_sum(bP[h][e]);
-              aQ[h][e] += byte_sum(bQ[h][e]);
-              bP[h][e] = bQ[h][e] = 0u;
-            }
+          ps.fold();
           since_fold = 0;
         }
       }
       if (!ok) break;
-      // the four lanes sharing an input pair hold disjoint samples
-#pragma unroll
-      for (int h = 0; h < 2; ++h)
-#pragma unroll
-        for (int e = 0; e < 2; ++e) {
-          aP[h][e] += __shfl_xor_sync(0xFFFFFFFFu, aP[h][e], 1);
-          aP[h][e] += __shfl_xor_sync(0xFFFFFFFFu, aP[h][e], 2);
-          aQ[h][e] += __shfl_xor_sync(0xFFFFFFFFu, aQ[h][e], 1);
-          aQ[h][e] += __shfl_xor_sync(0xFFFFFFFFu, aQ[h][e], 2);
-        }
+      ps.reduce();
       const int slot = ui & 1;
       if (!wait_or_abort(&s.sums_empty[slot], ((ui >> 1) & 1) ^ 1, lim, abort_flag)) {
         fail(s, prm.err, kErrWaitSumsEmpty);
         break;
       }
-      int* sums = s.sums + slot * 4 * kTile;
+      int* sl = s.sums + slot * kSlotInts;
       if ((lane & 3) == 0) {
 #pragma unroll
-        for (int h = 0; h < 2; ++h)
-#pragma unroll
-          for (int e = 0; e < 2; ++e) {
-            const int i = 16 * (2 * quad + h) + 2 * pj + e;
-            sums[i] = aP[h][e];            // each I input is owned by exactly one lane
-            sums[kTile + i] = aQ[h][e];
-          }
+        for (int e = 0; e < 2; ++e) {
+          const int i = 16 * ch + 2 * pj + e;   // each I input is owned by exactly one lane
+          sl[i] = ps.P[e];
+          sl[kTile + i] = ps.Q[e];
+        }
       }
       __syncwarp();
       if (lane == 0) mbar_arrive(&s.sums_full[slot]);
     }
   } else if (b_ordinal(warp) >= 0) {
     // ====================================================== B side -> shared planes
-    const int ut = b_ordinal(warp) * 32 + lane;  // 0..255
-    const int q = ut & 7, row = ut >> 3;       // 16-input chunk, time row within each step
-    const uint32_t off = sw128(kappa(row), q); // K row kappa(row) of the B planes
+    const int g = b_ordinal(warp);             // 16-input chunk within this CTA's half of J
+    const int q = 4 * static_cast<int>(rank) + g;  // the same chunk within the J tile
+    const int pj = lane >> 2;
+    const int n0 = 16 * g + pj;                // B rows of inputs 2 pj and 2 pj + 1: n0, n0 + 8
+    const int kq = lane & 3;                   // 8-byte K segment of each step
     int sit = 0, ui = 0;
     bool ok = true;
-    for (int u = blockIdx.x; u < prm.units && ok; u += gridDim.x, ++ui) {
-      int c, bi, bj;
-      decode_unit(u, npairs, c, bi, bj);
-      const bool diag = (bi == bj);
-      BSums sJ;
-      sJ.zero();
-      int since_flush = 0;
+    for (int u = cl; u < prm.units && ok; u += ncl, ++ui) {
+      const Unit t = decode_unit(u, per_chan, nt, rank);
+      const bool own_diag = (t.ti == t.tj);
+      PairSums ps;
+      ps.zero();
+      int since_fold = 0;
       for (int ks = 0; ks < nks; ks += kSteps, ++sit) {
         const int rst = sit % kRawStages, ost = sit % kOpStages;
         if (!wait_or_abort(&s.raw_full[rst], (sit / kRawStages) & 1, lim, abort_flag)) {
@@ -506,18 +614,18 @@ xcorr_tc8_kernel(const __grid_constant__ CUtensorMap tmap, TcParams prm) {
           ok = false;
           break;
         }
-        const uint8_t* rawJ = s.raw + rst * kRawStage + (diag ? 0 : kRawTile);
-        uint8_t* opB = s.op + ost * kOpStage;
+        const uint32_t rawJ_s = smem_u32(s.raw + rst * kRawStage + (own_diag ? 0 : kRawTile));
+        const uint32_t opB = smem_u32(s.op + ost * kOpStage);
 #pragma unroll
         for (int sub = 0; sub < kSteps; ++sub) {
-          const uint4 w = lds128(rawJ + sub * kRawSub + sw128(row, q));
-          uint4 re, im;
-          re.x = biased_re(w.x); re.y = biased_re(w.y); re.z = biased_re(w.z); re.w = biased_re(w.w);
-          im.x = biased_im(w.x); im.y = biased_im(w.y); im.z = biased_im(w.z); im.w = biased_im(w.w);
-          sJ.add(re, im);
-          uint8_t* b = opB + sub * 2 * kPlane;
-          sts128(b + off, re);
-          sts128(b + kPlane + off, im);
+          const Words w = unpack_block(rawJ_s + sub * kRawSub + sw128(lane, q), ps.bP, ps.bQ);
+          // K-major rows n0 and n0 + 8 (same swizzle phase), K bytes 32 sub + 8 kq
+          const int kb = 32 * sub + 8 * kq;
+          const uint32_t off = static_cast<uint32_t>(n0 * 128 + (((kb >> 4) ^ (n0 & 7)) << 4) + (kb & 15));
+          sts64(opB + off, w.re0, w.re1);
+          sts64(opB + off + 8 * 128, w.re2, w.re3);
+          sts64(opB + kPlane + off, w.im0, w.im1);
+          sts64(opB + kPlane + off + 8 * 128, w.im2, w.im3);
         }
         fence_proxy_async_smem();
         __syncwarp();
@@ -525,22 +633,32 @@ xcorr_tc8_kernel(const __grid_constant__ CUtensorMap tmap, TcParams prm) {
           mbar_arrive(&s.op_full[ost]);
           mbar_arrive(&s.raw_empty[rst]);
         }
-        if (++since_flush == 4) {  // 16 rows per 4 stages: byte lanes stay <= 240
-          sJ.flush();
-          since_flush = 0;
+        if (++since_fold == 2 || ks + kSteps >= nks) {
+          ps.fold();
+          since_fold = 0;
         }
       }
       if (!ok) break;
-      sJ.flush();
+      ps.reduce();
       const int slot = ui & 1;
       if (!wait_or_abort(&s.sums_empty[slot], ((ui >> 1) & 1) ^ 1, lim, abort_flag)) {
         fail(s, prm.err, kErrWaitSumsEmpty);
         break;
       }
-      int* sums = s.sums + slot * 4 * kTile;
-      if (!diag) sJ.publish(sums + 2 * kTile, sums + 3 * kTile, q);
+      int* sl = s.sums + slot * kSlotInts + 2 * kTile;
+      if ((lane & 3) == 0) {
+#pragma unroll
+        for (int e = 0; e < 2; ++e) {
+          const int j = 16 * g + 2 * pj + e;    // input offset within this CTA's half
+          sl[j] = ps.P[e];
+          sl[kHalf + j] = ps.Q[e];
+        }
+      }
       __syncwarp();
-      if (lane == 0) mbar_arrive(&s.sums_full[slot]);
+      if (lane == 0) {
+        mbar_arrive(&s.sums_full[slot]);
+        arrive_at(&s.sums_full[slot], peer);   // the partner's epilogue reads this half too
+      }
     }
   } else if (warp >= kEpiWarp0 && warp < kEpiWarp0 + 4) {
     // ====================================================== epilogue
@@ -548,51 +666,62 @@ xcorr_tc8_kernel(const __grid_constant__ CUtensorMap tmap, TcParams prm) {
     // reached equally often by all four warps); after an abort it only
     // skips work.
     const int quad = warp & 3;
-    const int L = 32 * quad + lane;                 // TMEM lane = accumulator row
-    const int il = lane_to_input(L);                // input offset of that row in I
+    const int L = 32 * quad + lane;                 // TMEM lane = accumulator row; also a column index
+    const int il = lane_to_input(L);                // input offset of row / column L in its tile
     const int T_pad = nks * kStep;
     const long long nbl = static_cast<long long>(prm.N) * (prm.N + 1) / 2;
     int2* stg = s.stage + quad * 32 * 32;
     bool ok = true;
     int ui = 0;
-    for (int u = blockIdx.x; u < prm.units; u += gridDim.x, ++ui) {
-      int c, bi, bj;
-      decode_unit(u, npairs, c, bi, bj);
-      const bool diag = (bi == bj);
+    for (int u = cl; u < prm.units; u += ncl, ++ui) {
+      const Unit t = decode_unit(u, per_chan, nt, rank);
       const int slot = ui & 1;
       if (ok && !wait_or_abort(&s.sums_full[slot], (ui >> 1) & 1, lim, abort_flag)) {
         fail(s, prm.err, kErrWaitSumsFull);
         ok = false;
       }
-      int* sums = s.sums + slot * 4 * kTile;
-      const int* PI = sums;
-      const int* QI = sums + kTile;
-      const int* PJ = diag ? sums : sums + 2 * kTile;
-      const int* QJ = diag ? sums + kTile : sums + 3 * kTile;
-      // Bias removal: every correction is a multiple of 8 below 2^27 and the
-      // corrected value an integer below 2^23, so one FFMA per value is exact.
+      const int* sl = s.sums + slot * kSlotInts;
+      float row_re = 0.f, row_im = 0.f;
       if (ok) {
-        s.colcorr[L] = static_cast<float>(-8 * (PJ[L] + QJ[L]));
-        s.colcorr[kTile + L] = static_cast<float>(-8 * (PJ[L] - QJ[L]));
+        // Bias removal: every correction is a multiple of 8 below 2^27 and the
+        // corrected value an integer below 2^23, so one FFMA per value is exact.
+        row_re = static_cast<float>(-8 * (sl[il] + sl[kTile + il]) + 128 * T_pad);
+        row_im = static_cast<float>(8 * (sl[il] - sl[kTile + il]));
+        // column L is J input il; its half (L / 64) is held by CTA L / 64
+        const uint32_t holder = static_cast<uint32_t>(L >> 6);
+        const int jo = il - kHalf * static_cast<int>(holder);
+        const int* pq = sl + 2 * kTile;
+        const int pjv = holder == rank ? pq[jo] : ld_peer(pq + jo, holder);
+        const int qjv = holder == rank ? pq[kHalf + jo] : ld_peer(pq + kHalf + jo, holder);
+        s.colcorr[L] = static_cast<float>(-8 * (pjv + qjv));
+        s.colcorr[kTile + L] = static_cast<float>(-8 * (pjv - qjv));
       }
       {
-        // this warp's 32 rows: packed-triangle row offsets (N <= 8192 fits int)
-        const int gi = bi * kTile + il;
+        // packed-triangle offsets of row L's and column L's inputs (N <= 8192 fits int)
+        const int gi = t.ti * kTile + il, gj = t.tj * kTile + il;
         s.rowoff[L] = gi < prm.N ? gi * (gi + 1) / 2 : 0;
+        s.coloff[L] = gj < prm.N ? gj * (gj + 1) / 2 : 0;
       }
       asm volatile("bar.sync 1, 128;" ::: "memory");
+      if (lane == 0) {   // this slot's own sums and the partner's half of J have been read
+        arrive_relaxed_at(&s.sums_empty[slot], rank);
+        arrive_relaxed_at(&s.sums_empty[slot], peer);
+      }
       if (ok && !wait_or_abort(s.acc_full, ui & 1, lim, abort_flag)) {
         fail(s, prm.err, kErrWaitAccFull);
         ok = false;
       }
       ok = __all_sync(0xFFFFFFFFu, ok);
       bool released = false;
-      if (ok) {
+      if (ok && t.write) {
         tc_fence_after();
-        const float row_re = static_cast<float>(-8 * (PI[il] + QI[il]) + 128 * T_pad);
-        const float row_im = static_cast<float>(8 * (PI[il] - QI[il]));
         const uint32_t t_row = tmem + (static_cast<uint32_t>(32 * quad) << 16);
-        const long long chan_base = static_cast<long long>(c) * nbl;
+        const long long chan_base = static_cast<long long>(t.c) * nbl;
+        int2* const acc = reinterpret_cast<int2*>(prm.acc) + chan_base;
+        // a tile strictly below the diagonal and inside N needs no checks
+        const bool full = !t.transposed && t.ti > t.tj && t.ti * kTile + kTile <= prm.N;
+        const bool tfull = t.transposed && t.tj * kTile + kTile <= prm.N;
+        const int gI = t.ti * kTile + il;           // this lane's row input
 #pragma unroll 1
         for (int cc = 0; cc < kTile; cc += 32) {
           uint32_t vre[32], vim[32];
@@ -600,87 +729,134 @@ xcorr_tc8_kernel(const __grid_constant__ CUtensorMap tmap, TcParams prm) {
           tmem_ld32(t_row + 128 + cc, vim);
           tmem_ld_wait();
           if (cc == kTile - 32) {
-            // all of D is in registers: the MMA warp may start the next unit
+            // all of D is in registers: the MMA may start the next unit
             tc_fence_before();
             __syncwarp();
-            if (lane == 0) mbar_arrive(s.acc_empty);
+            if (lane == 0) arrive_relaxed_at(s.acc_empty, 0);
             released = true;
           }
-          // this lane's row -> staging row `lane` (column index XOR lane)
+          if (!t.transposed) {
+            // this lane's row -> staging row `lane` (column index XOR lane)
 #pragma unroll
-          for (int k = 0; k < 32; ++k) {
-            const float cre = s.colcorr[cc + k], cim = s.colcorr[kTile + cc + k];
-            const int re = __float2int_rn(__fmaf_rn(__uint_as_float(vre[k]), 262144.0f, row_re + cre));
-            const int im = __float2int_rn(__fmaf_rn(__uint_as_float(vim[k]), 262144.0f, row_im + cim));
-            stg[lane * 32 + (k ^ lane)] = make_int2(re, im);
-          }
-          __syncwarp();
-          // 32 rows x 32 baselines: each row is 256 contiguous bytes of the accumulator
-          const int gj = bj * kTile + cc + lane;
-          const int* ro = s.rowoff + 32 * quad;
-          int2* accj = reinterpret_cast<int2*>(prm.acc) + chan_base + gj;
-          // a tile pair strictly below the diagonal and inside N needs no checks
-          const bool full = bi > bj && bi * kTile + kTile <= prm.N;
-          if (full && !prm.accumulate) {
-#pragma unroll 4
-            for (int r = 0; r < 32; ++r) accj[ro[r]] = stg[r * 32 + (lane ^ r)];
-          } else if (full) {
-#pragma unroll 4
-            for (int r = 0; r < 32; ++r) {
-              const int2 v = stg[r * 32 + (lane ^ r)];
-              int2* dst = accj + ro[r];
-              const int2 o = *dst;
-              *dst = make_int2(o.x + v.x, o.y + v.y);
+            for (int k = 0; k < 32; ++k) {
+              const float cre = s.colcorr[cc + k], cim = s.colcorr[kTile + cc + k];
+              const int re = __float2int_rn(__fmaf_rn(__uint_as_float(vre[k]), 262144.0f, row_re + cre));
+              const int im = __float2int_rn(__fmaf_rn(__uint_as_float(vim[k]), 262144.0f, row_im + cim));
+              stg[lane * 32 + (k ^ lane)] = make_int2(re, im);
             }
-          } else {
+            __syncwarp();
+            // 32 rows x 32 baselines: each row is 256 contiguous bytes (lanes permuted)
+            const int gj = t.tj * kTile + lane_to_input(cc + lane);
+            const int* ro = s.rowoff + 32 * quad;
+            int2* accj = acc + gj;
+            if (full && !prm.accumulate) {
 #pragma unroll 4
-            for (int r = 0; r < 32; ++r) {
-              const int gi = bi * kTile + lane_to_input(32 * quad + r);
-              if (gi < prm.N && gj <= gi && gj < prm.N) {
+              for (int r = 0; r < 32; ++r) accj[ro[r]] = stg[r * 32 + (lane ^ r)];
+            } else if (full) {
+#pragma unroll 4
+              for (int r = 0; r < 32; ++r) {
                 const int2 v = stg[r * 32 + (lane ^ r)];
                 int2* dst = accj + ro[r];
+                const int2 o = *dst;
+                *dst = make_int2(o.x + v.x, o.y + v.y);
+              }
+            } else {
+#pragma unroll 4
+              for (int r = 0; r < 32; ++r) {
+                const int gi = t.ti * kTile + lane_to_input(32 * quad + r);
+                if (gi < prm.N && gj <= gi) {
+                  const int2 v = stg[r * 32 + (lane ^ r)];
+                  int2* dst = accj + ro[r];
+                  if (prm.accumulate) {
+                    const int2 o = *dst;
+                    *dst = make_int2(o.x + v.x, o.y + v.y);
+                  } else {
+                    *dst = v;
+                  }
+                }
+              }
+            }
+            __syncwarp();
+          } else {
+            // transposed block: column cc + k is output row j, this lane's row
+            // input gI < j its column; the 32 lanes write 32 consecutive
+            // inputs of that row, conjugated
+            int2* acci = acc + gI;
+#pragma unroll
+            for (int k = 0; k < 32; ++k) {
+              const float cre = s.colcorr[cc + k], cim = s.colcorr[kTile + cc + k];
+              const int re = __float2int_rn(__fmaf_rn(__uint_as_float(vre[k]), 262144.0f, row_re + cre));
+              const int im = __float2int_rn(__fmaf_rn(__uint_as_float(vim[k]), 262144.0f, row_im + cim));
+              const bool in = tfull || (t.tj * kTile + lane_to_input(cc + k) < prm.N);
+              if (in) {
+                int2* dst = acci + s.coloff[cc + k];
                 if (prm.accumulate) {
                   const int2 o = *dst;
-                  *dst = make_int2(o.x + v.x, o.y + v.y);
+                  *dst = make_int2(o.x + re, o.y - im);
                 } else {
-                  *dst = v;
+                  *dst = make_int2(re, -im);
                 }
               }
             }
           }
-          __syncwarp();
         }
       }
       if (!released) {
+        // nothing (more) to read from D for this unit
+        if (ok) tc_fence_after();
+        tc_fence_before();
         __syncwarp();
-        if (lane == 0) mbar_arrive(s.acc_empty);
+        if (lane == 0) arrive_relaxed_at(s.acc_empty, 0);
       }
-      // all four warps are done with this slot's sums and column corrections
+      // all four warps are done with colcorr, rowoff, coloff and staging
       asm volatile("bar.sync 1, 128;" ::: "memory");
-      sums[L] = 0;
-      sums[kTile + L] = 0;
-      sums[2 * kTile + L] = 0;
-      sums[3 * kTile + L] = 0;
-      __syncwarp();
-      if (lane == 0) mbar_arrive(&s.sums_empty[slot]);
     }
   }
 
+  // Teardown: every MMA of the pair has completed (both CTAs' tensor memory
+  // and shared memory are read by it) before either CTA frees or leaves.
+  if (warp == 1 && lane == 0) {
+    if (!mbar_wait(s.final_bar, 0, lim)) atomicOr(prm.err, kErrWaitFinal);
+  }
   tc_fence_before();
   __syncthreads();
+  cluster_sync();
   tc_fence_after();
-  if (warp == 0) tmem_dealloc<kTmemCols>(tmem);
+  if (warp == 0) {
+    asm volatile("tcgen05.dealloc.cta_group::2.sync.aligned.b32 %0, %1;" ::"r"(tmem), "n"(kTmemCols));
+  }
 }
 
 }  // namespace tc8
 
 int tc8_smem_bytes() { return tc8::kSmemBytes; }
 
-cudaError_t launch_xcorr_tc8(const CUtensorMap* tmap, const TcParams& prm, int grid, cudaStream_t stream) {
+cudaError_t launch_xcorr_tc8(const CUtensorMap* tmap, TcParams prm, int max_ctas, cudaStream_t stream) {
   cudaError_t e = cudaFuncSetAttribute(tc8::xcorr_tc8_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        tc8::kSmemBytes);
   if (e != cudaSuccess) return e;
-  tc8::xcorr_tc8_kernel<<<grid, tc8::kThreads, tc8::kSmemBytes, stream>>>(*tmap, prm);
+  // clusters that can be resident at once (pairs of SMs), asked once per process
+  static int resident_clusters = -1;
+  if (resident_clusters < 0) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(2, 1, 1);
+    cfg.blockDim = dim3(tc8::kThreads, 1, 1);
+    cfg.dynamicSmemBytes = tc8::kSmemBytes;
+    int n = 0;
+    if (cudaOccupancyMaxActiveClusters(&n, tc8::xcorr_tc8_kernel, &cfg) != cudaSuccess || n < 1) {
+      cudaGetLastError();
+      n = 0;
+    }
+    resident_clusters = n;
+  }
+  const long long units = static_cast<long long>(prm.C) * tc8::pairs_per_channel(prm.nt);
+  if (units > 0x7FFFFFFFLL) return cudaErrorInvalidValue;
+  prm.units = static_cast<int>(units);
+  long long clusters = max_ctas / 2;
+  if (resident_clusters > 0 && resident_clusters < clusters) clusters = resident_clusters;
+  if (units < clusters) clusters = units;
+  if (clusters < 1) clusters = 1;
+  tc8::xcorr_tc8_kernel<<<static_cast<int>(2 * clusters), tc8::kThreads, tc8::kSmemBytes, stream>>>(*tmap, prm);
   return cudaGetLastError();
 }
 
