@@ -73,10 +73,10 @@ constexpr int kSteps = 4;                 // steps per pipeline stage (128 sampl
 constexpr int kRawSub = kStep * kTile;    // 4096 bytes: one step of one raw tile
 constexpr int kRawTile = kSteps * kRawSub;  // 16 KB TMA box: 128 time rows x 128 inputs
 #ifndef XE_TC8_RAW_STAGES
-#define XE_TC8_RAW_STAGES 3
+#define XE_TC8_RAW_STAGES 2
 #endif
 #ifndef XE_TC8_OP_STAGES
-#define XE_TC8_OP_STAGES 4
+#define XE_TC8_OP_STAGES 3
 #endif
 // Synchronisation happens once per stage of 4 steps: the tensor core's
 // instruction queue holds only a few MMAs, so every barrier check or commit
@@ -91,7 +91,8 @@ constexpr int kOpStage = 2 * kPlane;            // re plane, im plane
 constexpr int kRawStage = 2 * kRawTile;         // I box, J box
 constexpr int kOpBytes = kOpStages * kOpStage;
 constexpr int kRawBytes = kRawStages * kRawStage;
-constexpr int kStageBytes = 4 * 32 * 32 * 8;    // per epilogue warp: 32 rows x 32 int2
+constexpr int kStageBufs = 3;                   // accumulator chunks staged per epilogue warp
+constexpr int kStageBytes = 4 * kStageBufs * 32 * 32 * 8;  // per warp and chunk: 32 rows x 32 int2
 constexpr int kSlotInts = 2 * kTile + 2 * kHalf;  // P_I, Q_I (128 each), P_J, Q_J of this CTA's half
 constexpr int kSumsBytes = 2 * kSlotInts * 4 + 2 * kTile * 4 + 2 * kTile * 4;
 // 2 slots of sums, column corrections (re, im), row and column triangle offsets
@@ -131,7 +132,7 @@ enum ErrCode : int {
 struct Smem {
   uint8_t* op;     // [kOpStages][re, im][64 rows x 128 K bytes]  B planes (this CTA's half)
   uint8_t* raw;    // [kRawStages][2][kRawTile]
-  int2* stage;     // [4 warps][32 rows][32], column index XOR row
+  int2* stage;     // [4 warps][kStageBufs][32 rows][32], column index XOR row
   int* sums;       // [2][kSlotInts]
   float* colcorr;  // [2][128]: per-column bias corrections of the current unit (re, im)
   int* rowoff;     // [128]: packed-triangle offset i (i + 1) / 2 of each accumulator row's input i
@@ -329,16 +330,16 @@ __device__ __forceinline__ int lane_to_input(int L) {
   return (L & ~15) + (r < 8 ? 2 * r : 2 * (r - 8) + 1);
 }
 
-// One 32-time x 16-input block of a raw tile -> biased e4m3 words of the two
+// One 32-time x 16-input block of a raw tile (four 8x8 16-bit matrices read
+// transposed by ldmatrix) -> biased e4m3 words of the two
 // inputs 2p, 2p+1 (p = lane / 4): re0, re1 / im0, im1 hold 8 samples of
 // input 2p, re2, re3 / im2, im3 those of input 2p+1 (K bytes 8 (lane % 4)
 // to 8 (lane % 4) + 7 of the step).  Byte-lane sums go to bP / bQ.
 struct Words {
   uint32_t re0, re1, re2, re3, im0, im1, im2, im3;
 };
-__device__ __forceinline__ Words unpack_block(uint32_t addr, uint32_t (&bP)[2], uint32_t (&bQ)[2]) {
-  uint32_t d0, d1, d2, d3;
-  ldsm_x4_trans(addr, d0, d1, d2, d3);
+__device__ __forceinline__ Words unpack_words(const uint32_t (&d)[4], uint32_t (&bP)[2], uint32_t (&bQ)[2]) {
+  const uint32_t d0 = d[0], d1 = d[1], d2 = d[2], d3 = d[3];
   const uint32_t w0 = __byte_perm(d0, d1, 0x6420), w1 = __byte_perm(d2, d3, 0x6420);
   const uint32_t w2 = __byte_perm(d0, d1, 0x7531), w3 = __byte_perm(d2, d3, 0x7531);
   Words o;
@@ -379,6 +380,21 @@ struct PairSums {
     }
   }
 };
+
+// Bias removal of one 32-column chunk of this lane's accumulator row into a
+// staging buffer (row `lane`, column index XOR lane).  Every correction is a
+// multiple of 8 below 2^27 and the corrected value an integer below 2^23, so
+// one FFMA per value is exact.
+__device__ __forceinline__ void stage_chunk(int2* buf, const uint32_t (&vre)[32], const uint32_t (&vim)[32],
+                                            const float* colcorr, float row_re, float row_im, int lane) {
+#pragma unroll
+  for (int k = 0; k < 32; ++k) {
+    const float cre = colcorr[k], cim = colcorr[kTile + k];
+    const int re = __float2int_rn(__fmaf_rn(__uint_as_float(vre[k]), 262144.0f, row_re + cre));
+    const int im = __float2int_rn(__fmaf_rn(__uint_as_float(vim[k]), 262144.0f, row_im + cim));
+    buf[lane * 32 + (k ^ lane)] = make_int2(re, im);
+  }
+}
 
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
 xcorr_tc8_kernel(const __grid_constant__ CUtensorMap tmap, TcParams prm) {
@@ -544,16 +560,22 @@ xcorr_tc8_kernel(const __grid_constant__ CUtensorMap tmap, TcParams prm) {
           ok = false;
           break;
         }
+        // the four transposing loads first (their latencies overlap), while
+        // the MMA may still hold the operand stage
+        const uint32_t rawI_s = smem_u32(s.raw + rst * kRawStage);
+        uint32_t dv[kSteps][4];
+#pragma unroll
+        for (int sub = 0; sub < kSteps; ++sub)
+          ldsm_x4_trans(rawI_s + sub * kRawSub + sw128(lane, ch), dv[sub][0], dv[sub][1], dv[sub][2], dv[sub][3]);
         if (!wait_or_abort(&s.op_empty[ost], ((sit / kOpStages) & 1) ^ 1, lim, abort_flag)) {
           fail(s, prm.err, kErrWaitOpEmpty);
           ok = false;
           break;
         }
-        const uint32_t rawI_s = smem_u32(s.raw + rst * kRawStage);
         const uint32_t ta0 = tmem + kTmemA0 + kTmemAStage * ost + lane_off;
 #pragma unroll
         for (int sub = 0; sub < kSteps; ++sub) {
-          const Words w = unpack_block(rawI_s + sub * kRawSub + sw128(lane, ch), ps.bP, ps.bQ);
+          const Words w = unpack_words(dv[sub], ps.bP, ps.bQ);
           tmem_st_16x256b_x2(ta0 + 16 * sub, w.re0, w.re1, w.re2, w.re3, w.im0, w.im1, w.im2, w.im3);
         }
         tmem_st_wait();
@@ -609,16 +631,20 @@ xcorr_tc8_kernel(const __grid_constant__ CUtensorMap tmap, TcParams prm) {
           ok = false;
           break;
         }
+        const uint32_t rawJ_s = smem_u32(s.raw + rst * kRawStage + (own_diag ? 0 : kRawTile));
+        uint32_t dv[kSteps][4];
+#pragma unroll
+        for (int sub = 0; sub < kSteps; ++sub)
+          ldsm_x4_trans(rawJ_s + sub * kRawSub + sw128(lane, q), dv[sub][0], dv[sub][1], dv[sub][2], dv[sub][3]);
         if (!wait_or_abort(&s.op_empty[ost], ((sit / kOpStages) & 1) ^ 1, lim, abort_flag)) {
           fail(s, prm.err, kErrWaitOpEmpty);
           ok = false;
           break;
         }
-        const uint32_t rawJ_s = smem_u32(s.raw + rst * kRawStage + (own_diag ? 0 : kRawTile));
         const uint32_t opB = smem_u32(s.op + ost * kOpStage);
 #pragma unroll
         for (int sub = 0; sub < kSteps; ++sub) {
-          const Words w = unpack_block(rawJ_s + sub * kRawSub + sw128(lane, q), ps.bP, ps.bQ);
+          const Words w = unpack_words(dv[sub], ps.bP, ps.bQ);
           // K-major rows n0 and n0 + 8 (same swizzle phase), K bytes 32 sub + 8 kq
           const int kb = 32 * sub + 8 * kq;
           const uint32_t off = static_cast<uint32_t>(n0 * 128 + (((kb >> 4) ^ (n0 & 7)) << 4) + (kb & 15));
@@ -670,7 +696,7 @@ xcorr_tc8_kernel(const __grid_constant__ CUtensorMap tmap, TcParams prm) {
     const int il = lane_to_input(L);                // input offset of row / column L in its tile
     const int T_pad = nks * kStep;
     const long long nbl = static_cast<long long>(prm.N) * (prm.N + 1) / 2;
-    int2* stg = s.stage + quad * 32 * 32;
+    int2* stg = s.stage + quad * kStageBufs * 32 * 32;
     bool ok = true;
     int ui = 0;
     for (int u = cl; u < prm.units; u += ncl, ++ui) {
@@ -683,8 +709,7 @@ xcorr_tc8_kernel(const __grid_constant__ CUtensorMap tmap, TcParams prm) {
       const int* sl = s.sums + slot * kSlotInts;
       float row_re = 0.f, row_im = 0.f;
       if (ok) {
-        // Bias removal: every correction is a multiple of 8 below 2^27 and the
-        // corrected value an integer below 2^23, so one FFMA per value is exact.
+        // bias corrections of this lane's row and of column L (see stage_chunk)
         row_re = static_cast<float>(-8 * (sl[il] + sl[kTile + il]) + 128 * T_pad);
         row_im = static_cast<float>(8 * (sl[il] - sl[kTile + il]));
         // column L is J input il; its half (L / 64) is held by CTA L / 64
@@ -722,40 +747,42 @@ xcorr_tc8_kernel(const __grid_constant__ CUtensorMap tmap, TcParams prm) {
         const bool full = !t.transposed && t.ti > t.tj && t.ti * kTile + kTile <= prm.N;
         const bool tfull = t.transposed && t.tj * kTile + kTile <= prm.N;
         const int gI = t.ti * kTile + il;           // this lane's row input
+        const int* ro = s.rowoff + 32 * quad;
+        // D leaves tensor memory first: chunks 0-2 (32 columns each) corrected
+        // into shared staging, chunk 3 into registers; then D is released and
+        // the global writes run while the MMA works on the next unit.
+        uint32_t vre[32], vim[32];
 #pragma unroll 1
         for (int cc = 0; cc < kTile; cc += 32) {
-          uint32_t vre[32], vim[32];
           tmem_ld32(t_row + cc, vre);
           tmem_ld32(t_row + 128 + cc, vim);
           tmem_ld_wait();
-          if (cc == kTile - 32) {
-            // all of D is in registers: the MMA may start the next unit
-            tc_fence_before();
+          if (cc < kStageBufs * 32) stage_chunk(stg + (cc >> 5) * 1024, vre, vim, s.colcorr + cc, row_re, row_im, lane);
+        }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) arrive_relaxed_at(s.acc_empty, 0);
+        released = true;
+#pragma unroll 1
+        for (int b = 0; b < 4; ++b) {
+          const int cc = 32 * b;
+          const int2* sb = stg + (b == 3 ? 0 : b) * 1024;
+          if (b == 3) {  // buffer 0 has been written out: chunk 3 goes there
             __syncwarp();
-            if (lane == 0) arrive_relaxed_at(s.acc_empty, 0);
-            released = true;
+            stage_chunk(stg, vre, vim, s.colcorr + cc, row_re, row_im, lane);
           }
+          __syncwarp();
           if (!t.transposed) {
-            // this lane's row -> staging row `lane` (column index XOR lane)
-#pragma unroll
-            for (int k = 0; k < 32; ++k) {
-              const float cre = s.colcorr[cc + k], cim = s.colcorr[kTile + cc + k];
-              const int re = __float2int_rn(__fmaf_rn(__uint_as_float(vre[k]), 262144.0f, row_re + cre));
-              const int im = __float2int_rn(__fmaf_rn(__uint_as_float(vim[k]), 262144.0f, row_im + cim));
-              stg[lane * 32 + (k ^ lane)] = make_int2(re, im);
-            }
-            __syncwarp();
             // 32 rows x 32 baselines: each row is 256 contiguous bytes (lanes permuted)
             const int gj = t.tj * kTile + lane_to_input(cc + lane);
-            const int* ro = s.rowoff + 32 * quad;
             int2* accj = acc + gj;
             if (full && !prm.accumulate) {
 #pragma unroll 4
-              for (int r = 0; r < 32; ++r) accj[ro[r]] = stg[r * 32 + (lane ^ r)];
+              for (int r = 0; r < 32; ++r) accj[ro[r]] = sb[r * 32 + (lane ^ r)];
             } else if (full) {
 #pragma unroll 4
               for (int r = 0; r < 32; ++r) {
-                const int2 v = stg[r * 32 + (lane ^ r)];
+                const int2 v = sb[r * 32 + (lane ^ r)];
                 int2* dst = accj + ro[r];
                 const int2 o = *dst;
                 *dst = make_int2(o.x + v.x, o.y + v.y);
@@ -765,7 +792,7 @@ xcorr_tc8_kernel(const __grid_constant__ CUtensorMap tmap, TcParams prm) {
               for (int r = 0; r < 32; ++r) {
                 const int gi = t.ti * kTile + lane_to_input(32 * quad + r);
                 if (gi < prm.N && gj <= gi) {
-                  const int2 v = stg[r * 32 + (lane ^ r)];
+                  const int2 v = sb[r * 32 + (lane ^ r)];
                   int2* dst = accj + ro[r];
                   if (prm.accumulate) {
                     const int2 o = *dst;
@@ -776,30 +803,27 @@ xcorr_tc8_kernel(const __grid_constant__ CUtensorMap tmap, TcParams prm) {
                 }
               }
             }
-            __syncwarp();
           } else {
             // transposed block: column cc + k is output row j, this lane's row
             // input gI < j its column; the 32 lanes write 32 consecutive
             // inputs of that row, conjugated
             int2* acci = acc + gI;
-#pragma unroll
+#pragma unroll 4
             for (int k = 0; k < 32; ++k) {
-              const float cre = s.colcorr[cc + k], cim = s.colcorr[kTile + cc + k];
-              const int re = __float2int_rn(__fmaf_rn(__uint_as_float(vre[k]), 262144.0f, row_re + cre));
-              const int im = __float2int_rn(__fmaf_rn(__uint_as_float(vim[k]), 262144.0f, row_im + cim));
-              const bool in = tfull || (t.tj * kTile + lane_to_input(cc + k) < prm.N);
-              if (in) {
+              if (tfull || t.tj * kTile + lane_to_input(cc + k) < prm.N) {
+                const int2 v = sb[lane * 32 + (k ^ lane)];
                 int2* dst = acci + s.coloff[cc + k];
                 if (prm.accumulate) {
                   const int2 o = *dst;
-                  *dst = make_int2(o.x + re, o.y - im);
+                  *dst = make_int2(o.x + v.x, o.y - v.y);
                 } else {
-                  *dst = make_int2(re, -im);
+                  *dst = make_int2(v.x, -v.y);
                 }
               }
             }
           }
         }
+        __syncwarp();
       }
       if (!released) {
         // nothing (more) to read from D for this unit
