@@ -387,12 +387,19 @@ struct PairSums {
 // one FFMA per value is exact.
 __device__ __forceinline__ void stage_chunk(int2* buf, const uint32_t (&vre)[32], const uint32_t (&vim)[32],
                                             const float* colcorr, float row_re, float row_im, int lane) {
+  const float4* cre4 = reinterpret_cast<const float4*>(colcorr);
+  const float4* cim4 = reinterpret_cast<const float4*>(colcorr + kTile);
 #pragma unroll
-  for (int k = 0; k < 32; ++k) {
-    const float cre = colcorr[k], cim = colcorr[kTile + k];
-    const int re = __float2int_rn(__fmaf_rn(__uint_as_float(vre[k]), 262144.0f, row_re + cre));
-    const int im = __float2int_rn(__fmaf_rn(__uint_as_float(vim[k]), 262144.0f, row_im + cim));
-    buf[lane * 32 + (k ^ lane)] = make_int2(re, im);
+  for (int k4 = 0; k4 < 8; ++k4) {
+    const float4 cr = cre4[k4], ci = cim4[k4];
+    const float crv[4] = {cr.x, cr.y, cr.z, cr.w}, civ[4] = {ci.x, ci.y, ci.z, ci.w};
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const int k = 4 * k4 + e;
+      const int re = __float2int_rn(__fmaf_rn(__uint_as_float(vre[k]), 262144.0f, row_re + crv[e]));
+      const int im = __float2int_rn(__fmaf_rn(__uint_as_float(vim[k]), 262144.0f, row_im + civ[e]));
+      buf[lane * 32 + (k ^ lane)] = make_int2(re, im);
+    }
   }
 }
 
