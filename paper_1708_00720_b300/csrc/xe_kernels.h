@@ -31,11 +31,13 @@ int tc_threads();
 cudaError_t launch_xcorr_tc(int eb, const CUtensorMap* tmap, const TcParams& prm, int grid,
                             cudaStream_t stream);
 
-// e4m3 X-engine on pairs of CTAs (tmap: uint8 {N, C, T}, box {128, 1, 128},
-// 128-byte swizzle).  prm.units is set here (channels x pair units); the grid
-// is at most max_ctas CTAs (an even number).
+// e4m3 X-engine on pairs of CTAs.  Both maps view the gulp as uint8
+// {N, C, T}: tmap_i with box {128, 1, 128} and the 128-byte swizzle, tmap_j
+// with box {64, 1, 128} and the 64-byte swizzle.  prm.units is set here
+// (channels x pair units); the grid is at most max_ctas CTAs (an even number).
 int tc8_smem_bytes();
-cudaError_t launch_xcorr_tc8(const CUtensorMap* tmap, TcParams prm, int max_ctas, cudaStream_t stream);
+cudaError_t launch_xcorr_tc8(const CUtensorMap* tmap_i, const CUtensorMap* tmap_j, TcParams prm, int max_ctas,
+                             cudaStream_t stream);
 
 // Plain CUDA-core correlator (int8 dot products into int32), the baseline.
 cudaError_t launch_xcorr_cudacore(const uint8_t* gulp, int T, int C, int N, int32_t* acc,

@@ -130,14 +130,18 @@ extern "C" XE_API xe_status xe_correlate_noalloc(const uint8_t* d_gulp, int ntim
   for (int t0 = 0; t0 < ntime; t0 += kLaunchNtime) {
     const int T = (ntime - t0) < kLaunchNtime ? (ntime - t0) : kLaunchNtime;
     const uint8_t* slice = d_gulp + static_cast<size_t>(t0) * row_bytes;
-    CUtensorMap map;
+    CUtensorMap map, map_j;
     cuuint64_t dims[3] = {static_cast<cuuint64_t>(n_input), static_cast<cuuint64_t>(n_chan),
                           static_cast<cuuint64_t>(T)};
     cuuint64_t strides[2] = {static_cast<cuuint64_t>(n_input), static_cast<cuuint64_t>(row_bytes)};
-    cuuint32_t box[3] = {128, 1, 128};
+    cuuint32_t box[3] = {128, 1, 128};       // I tiles, 128-byte swizzle
+    cuuint32_t box_j[3] = {64, 1, 128};      // half J tiles, 64-byte swizzle
     cuuint32_t estr[3] = {1, 1, 1};
     if (enc(&map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 3, const_cast<uint8_t*>(slice), dims, strides, box, estr,
             CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+            CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS ||
+        enc(&map_j, CU_TENSOR_MAP_DATA_TYPE_UINT8, 3, const_cast<uint8_t*>(slice), dims, strides, box_j, estr,
+            CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
             CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
       return XE_ERR_CUDA;
     xe::TcParams prm;
@@ -150,7 +154,7 @@ extern "C" XE_API xe_status xe_correlate_noalloc(const uint8_t* d_gulp, int ntim
     prm.acc = d_acc;
     prm.err = d_err;
     prm.timeout_ns = kWaitTimeoutNs;
-    if (xe::launch_xcorr_tc8(&map, prm, sms, s) != cudaSuccess) return XE_ERR_CUDA;
+    if (xe::launch_xcorr_tc8(&map, &map_j, prm, sms, s) != cudaSuccess) return XE_ERR_CUDA;
   }
   cudaError_t e = (out_type == XE_OUT_CI32)
                       ? cudaMemcpyAsync(d_vis, d_acc, out_bytes, cudaMemcpyDeviceToDevice, s)

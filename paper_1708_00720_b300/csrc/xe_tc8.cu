@@ -28,8 +28,9 @@
 // CTA 1 repeats its partner's tile and writes nothing.
 //
 // Per step (32 samples) of a unit:
-//  * TMA loads the raw 32 x 128-byte time x input tiles of I and J into
-//    shared memory with the 128-byte swizzle (J is skipped when I == J).
+//  * TMA loads the raw time x input tile of I (128-byte rows, 128-byte
+//    swizzle) and this CTA's half of J (64-byte rows, 64-byte swizzle) into
+//    shared memory; J is skipped when I == J.
 //  * A side (two warps per TMEM lane quadrant, one per 16-input chunk):
 //    ldmatrix.x4.trans reads a 32-time x 16-input block as 16-bit pairs,
 //    four byte permutes regroup it so that each 32-bit word holds four
@@ -72,11 +73,12 @@ constexpr int kStep = 32;                 // samples per MMA step (K = 32 e4m3)
 constexpr int kSteps = 4;                 // steps per pipeline stage (128 samples)
 constexpr int kRawSub = kStep * kTile;    // 4096 bytes: one step of one raw tile
 constexpr int kRawTile = kSteps * kRawSub;  // 16 KB TMA box: 128 time rows x 128 inputs
+constexpr int kRawHalf = kRawTile / 2;      // 8 KB TMA box: 128 time rows x this CTA's 64 J inputs
 #ifndef XE_TC8_RAW_STAGES
 #define XE_TC8_RAW_STAGES 2
 #endif
 #ifndef XE_TC8_OP_STAGES
-#define XE_TC8_OP_STAGES 3
+#define XE_TC8_OP_STAGES 4
 #endif
 // Synchronisation happens once per stage of 4 steps: the tensor core's
 // instruction queue holds only a few MMAs, so every barrier check or commit
@@ -88,7 +90,7 @@ constexpr int kRawStages = XE_TC8_RAW_STAGES;
 constexpr int kOpStages = XE_TC8_OP_STAGES;
 constexpr int kPlane = kHalf * kSteps * kStep;  // 8 KB: 64 rows x 128 K bytes, K-major
 constexpr int kOpStage = 2 * kPlane;            // re plane, im plane
-constexpr int kRawStage = 2 * kRawTile;         // I box, J box
+constexpr int kRawStage = kRawTile + kRawHalf;  // I box (128-byte rows), half J box (64-byte rows)
 constexpr int kOpBytes = kOpStages * kOpStage;
 constexpr int kRawBytes = kRawStages * kRawStage;
 constexpr int kStageBufs = 3;                   // accumulator chunks staged per epilogue warp
@@ -131,7 +133,7 @@ enum ErrCode : int {
 
 struct Smem {
   uint8_t* op;     // [kOpStages][re, im][64 rows x 128 K bytes]  B planes (this CTA's half)
-  uint8_t* raw;    // [kRawStages][2][kRawTile]
+  uint8_t* raw;    // [kRawStages][I: kRawTile | J half: kRawHalf]
   int2* stage;     // [4 warps][kStageBufs][32 rows][32], column index XOR row
   int* sums;       // [2][kSlotInts]
   float* colcorr;  // [2][128]: per-column bias corrections of the current unit (re, im)
@@ -404,7 +406,7 @@ __device__ __forceinline__ void stage_chunk(int2* buf, const uint32_t (&vre)[32]
 }
 
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
-xcorr_tc8_kernel(const __grid_constant__ CUtensorMap tmap, TcParams prm) {
+xcorr_tc8_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CUtensorMap tmap_j, TcParams prm) {
   extern __shared__ uint8_t smem_raw[];
   uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                              ~static_cast<uintptr_t>(1023));
@@ -439,6 +441,7 @@ xcorr_tc8_kernel(const __grid_constant__ CUtensorMap tmap, TcParams prm) {
     *s.abort_flag = 0;
     mbar_fence_init();
     tma_prefetch_desc(&tmap);
+    tma_prefetch_desc(&tmap_j);
   }
   if (warp == 0) {
     // one warp of each CTA of the pair allocates together: same columns in both
@@ -473,8 +476,9 @@ xcorr_tc8_kernel(const __grid_constant__ CUtensorMap tmap, TcParams prm) {
             mbar_arrive_expect_tx(&s.raw_full[st], kRawTile);
             tma_load_3d(dst, &tmap, &s.raw_full[st], t.ti * kTile, t.c, ks * kStep);
           } else if (!own_diag) {
-            mbar_arrive_expect_tx(&s.raw_full[st], kRawTile);
-            tma_load_3d(dst, &tmap, &s.raw_full[st], t.tj * kTile, t.c, ks * kStep);
+            mbar_arrive_expect_tx(&s.raw_full[st], kRawHalf);
+            tma_load_3d(dst, &tmap_j, &s.raw_full[st], t.tj * kTile + kHalf * static_cast<int>(rank), t.c,
+                        ks * kStep);
           } else {
             mbar_arrive(&s.raw_full[st]);    // the I tile serves as J
           }
@@ -638,11 +642,16 @@ xcorr_tc8_kernel(const __grid_constant__ CUtensorMap tmap, TcParams prm) {
           ok = false;
           break;
         }
-        const uint32_t rawJ_s = smem_u32(s.raw + rst * kRawStage + (own_diag ? 0 : kRawTile));
+        // this CTA's 64 J inputs: 64-byte rows of the half tile (chunk g at
+        // g XOR ((t >> 1) & 3) in row t), or chunk q of the I tile when I == J
+        const uint32_t raw_s = smem_u32(s.raw + rst * kRawStage);
+        const uint32_t rowJ = own_diag ? raw_s + sw128(lane, q)
+                                       : raw_s + kRawTile + lane * 64 + ((g ^ ((lane >> 1) & 3)) << 4);
+        const uint32_t subJ = own_diag ? kRawSub : kRawSub / 2;
         uint32_t dv[kSteps][4];
 #pragma unroll
         for (int sub = 0; sub < kSteps; ++sub)
-          ldsm_x4_trans(rawJ_s + sub * kRawSub + sw128(lane, q), dv[sub][0], dv[sub][1], dv[sub][2], dv[sub][3]);
+          ldsm_x4_trans(rowJ + sub * subJ, dv[sub][0], dv[sub][1], dv[sub][2], dv[sub][3]);
         if (!wait_or_abort(&s.op_empty[ost], ((sit / kOpStages) & 1) ^ 1, lim, abort_flag)) {
           fail(s, prm.err, kErrWaitOpEmpty);
           ok = false;
@@ -862,7 +871,8 @@ xcorr_tc8_kernel(const __grid_constant__ CUtensorMap tmap, TcParams prm) {
 
 int tc8_smem_bytes() { return tc8::kSmemBytes; }
 
-cudaError_t launch_xcorr_tc8(const CUtensorMap* tmap, TcParams prm, int max_ctas, cudaStream_t stream) {
+cudaError_t launch_xcorr_tc8(const CUtensorMap* tmap_i, const CUtensorMap* tmap_j, TcParams prm, int max_ctas,
+                             cudaStream_t stream) {
   cudaError_t e = cudaFuncSetAttribute(tc8::xcorr_tc8_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        tc8::kSmemBytes);
   if (e != cudaSuccess) return e;
@@ -887,7 +897,8 @@ cudaError_t launch_xcorr_tc8(const CUtensorMap* tmap, TcParams prm, int max_ctas
   if (resident_clusters > 0 && resident_clusters < clusters) clusters = resident_clusters;
   if (units < clusters) clusters = units;
   if (clusters < 1) clusters = 1;
-  tc8::xcorr_tc8_kernel<<<static_cast<int>(2 * clusters), tc8::kThreads, tc8::kSmemBytes, stream>>>(*tmap, prm);
+  tc8::xcorr_tc8_kernel<<<static_cast<int>(2 * clusters), tc8::kThreads, tc8::kSmemBytes, stream>>>(*tmap_i, *tmap_j,
+                                                                                                  prm);
   return cudaGetLastError();
 }
 
