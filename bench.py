@@ -53,7 +53,7 @@ CALIB_METRIC = "gain-calibration chi^2 + adjoint gradient: visibility baselines 
 METRIC = "X-engine complex-MAC TOPS & % FP8 peak at 512 inputs vs plain int32 kernel"
 KERNEL_SOURCES = {
     "xcorr_tc_fp8": ["paper_1708_00720_b300/csrc/xe_tc8.cu", "paper_1708_00720_b300/csrc/xe_ptx.cuh"],
-    "xcorr_tc_fp16": ["paper_1708_00720_b300/csrc/xe_tc.cu", "paper_1708_00720_b300/csrc/xe_ptx.cuh"],
+    "xcorr_tc_fp16": ["paper_1708_00720_b300/csrc/xe_tc8.cu", "paper_1708_00720_b300/csrc/xe_ptx.cuh"],
     "xcorr_cudacore": ["paper_1708_00720_b300/csrc/xe_cudacore.cu"],
     "calib_pass": ["paper_1708_00720_b300/csrc/xe_calib.cu"],
     "beam_kernel": ["paper_1708_00720_b300/csrc/xe_beam.cu", "paper_1708_00720_b300/csrc/xe_ptx.cuh"],

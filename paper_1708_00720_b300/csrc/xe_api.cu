@@ -72,11 +72,11 @@ xe_status cuda_fail(xe_plan* p, cudaError_t e, const char* what) {
 
 bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
 
-// Encode the tensor map of one gulp slice: uint8 {N, C, T}.  kind 0: box
-// {128, 1, 32}, no swizzle (f16 kernel); kind 1: box {128, 1, 128} with the
-// 128-byte shared-memory swizzle (e4m3 kernel, I tiles); kind 2: box
-// {64, 1, 128} with the 64-byte swizzle (e4m3 kernel, half J tiles).
-xe_status encode_gulp_map(xe_plan* p, const uint8_t* gulp, int T, int kind, CUtensorMap* map) {
+// Encode the tensor map of one gulp slice: uint8 {N, C, T}, box
+// {box_x inputs, 1 channel, box_t samples}, shared-memory swizzle of
+// swizzle_bytes (128 or 64).
+xe_status encode_gulp_map(xe_plan* p, const uint8_t* gulp, int T, unsigned box_x, unsigned box_t, int swizzle_bytes,
+                          CUtensorMap* map) {
   EncodeTiledFn enc = get_encode_fn();
   if (!enc) {
     p->last_error = "cuTensorMapEncodeTiled entry point unavailable";
@@ -86,11 +86,11 @@ xe_status encode_gulp_map(xe_plan* p, const uint8_t* gulp, int T, int kind, CUte
                         static_cast<cuuint64_t>(T)};
   cuuint64_t strides[2] = {static_cast<cuuint64_t>(p->N),
                            static_cast<cuuint64_t>(p->N) * static_cast<cuuint64_t>(p->C)};
-  cuuint32_t box[3] = {kind == 2 ? 64u : 128u, 1, kind == 0 ? 32u : 128u};
+  cuuint32_t box[3] = {box_x, 1, box_t};
   cuuint32_t estr[3] = {1, 1, 1};
   CUresult r = enc(map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 3, const_cast<uint8_t*>(gulp), dims, strides,
                    box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                   kind == 1 ? CU_TENSOR_MAP_SWIZZLE_128B : (kind == 2 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_NONE),
+                   swizzle_bytes == 128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   if (r != CUDA_SUCCESS) {
     char buf[96];
@@ -145,27 +145,25 @@ xe_status enqueue_correlate(xe_plan* p, const uint8_t* d_gulp, int ntime, int ac
   }
   const int eb = (p->op == XE_OPERAND_FP8_E4M3) ? 1 : 2;
   const int nt = (p->N + 127) / 128;
-  const long long units = static_cast<long long>(p->C) * nt * (nt + 1) / 2;
-  const int grid = static_cast<int>(units < p->num_sms ? units : p->num_sms);
+  const unsigned rows = eb == 1 ? 128u : 64u;   // samples per pipeline stage (one TMA box)
   for (int t0 = 0; t0 < ntime; t0 += kTcMaxLaunchNtime) {
     const int T = (ntime - t0) < kTcMaxLaunchNtime ? (ntime - t0) : kTcMaxLaunchNtime;
     CUtensorMap map, map_j;
     const uint8_t* slice = d_gulp + static_cast<size_t>(t0) * row_bytes;
-    xe_status st = encode_gulp_map(p, slice, T, eb == 1 ? 1 : 0, &map);
-    if (st == XE_OK && eb == 1) st = encode_gulp_map(p, slice, T, 2, &map_j);
+    xe_status st = encode_gulp_map(p, slice, T, 128, rows, 128, &map);       // I tiles
+    if (st == XE_OK) st = encode_gulp_map(p, slice, T, 64, rows, 64, &map_j);  // half J tiles
     if (st != XE_OK) return st;
     xe::TcParams prm;
     prm.N = p->N;
     prm.C = p->C;
     prm.nt = nt;
-    prm.units = static_cast<int>(units);
-    prm.nks = (eb == 1) ? 4 * ((T + 127) / 128) : (T + 31) / 32;  // e4m3 kernel: whole 4-step TMA boxes
+    prm.units = 0;  // set by the launcher
+    prm.nks = static_cast<int>((T + rows - 1) / rows * (rows / 32));   // whole stages of 32-sample steps
     prm.accumulate = (accumulate || t0 > 0) ? 1 : 0;
     prm.acc = p->d_acc;
     prm.err = p->d_err;
     prm.timeout_ns = kWaitTimeoutNs;
-    cudaError_t e = (eb == 1) ? xe::launch_xcorr_tc8(&map, &map_j, prm, p->num_sms, stream)
-                              : xe::launch_xcorr_tc(eb, &map, prm, grid, stream);
+    cudaError_t e = xe::launch_xcorr_pair(eb, &map, &map_j, prm, p->num_sms, stream);
     if (e != cudaSuccess) return cuda_fail(p, e, "tcgen05 launch");
     ++p->launches;
   }

@@ -13,31 +13,24 @@ struct TcParams {
   int N;                  // inputs
   int C;                  // channels
   int nt;                 // 128-input tiles per side, ceil(N / 128)
-  int units;              // C * nt (nt + 1) / 2 work units (channel, tile pair)
-  int nks;                // 32-sample steps, ceil(T / 32), T <= 32768
+  int units;              // channels x pair units (set by the launcher)
+  int nks;                // 32-sample steps, whole pipeline stages, T <= 32768
   int accumulate;         // 1: add into acc; 0: overwrite
   int32_t* acc;           // [C][N (N + 1) / 2][2] int32 accumulator
   int* err;               // device error word (bit mask of timed-out waits)
   unsigned long long timeout_ns;  // bound on every device-side wait
 };
 
-// Shared-memory bytes and block size of the tcgen05 kernel (eb = operand
-// bytes per element: 1 = e4m3, 2 = f16).
-int tc_smem_bytes(int eb);
-int tc_threads();
-
-// One launch of the tcgen05 X-engine over a gulp described by tmap (uint8,
-// dims {N, C, T}, box {128, 1, 32}).
-cudaError_t launch_xcorr_tc(int eb, const CUtensorMap* tmap, const TcParams& prm, int grid,
-                            cudaStream_t stream);
-
-// e4m3 X-engine on pairs of CTAs.  Both maps view the gulp as uint8
-// {N, C, T}: tmap_i with box {128, 1, 128} and the 128-byte swizzle, tmap_j
-// with box {64, 1, 128} and the 64-byte swizzle.  prm.units is set here
-// (channels x pair units); the grid is at most max_ctas CTAs (an even number).
-int tc8_smem_bytes();
-cudaError_t launch_xcorr_tc8(const CUtensorMap* tmap_i, const CUtensorMap* tmap_j, TcParams prm, int max_ctas,
-                             cudaStream_t stream);
+// Tensor-core X-engine on pairs of CTAs, operand width eb (1: e4m3, 2:
+// float16).  Both maps view the gulp as uint8 {N, C, T}: tmap_i with box
+// {128, 1, R} and the 128-byte swizzle, tmap_j with box {64, 1, R} and the
+// 64-byte swizzle, R = 128 time rows for e4m3 and 64 for float16.
+// prm.nks must be a multiple of 4 (e4m3) or 2 (float16) 32-sample steps;
+// prm.units is set here (channels x pair units); the grid is at most max_ctas
+// CTAs (an even number).
+int tc8_smem_bytes(int eb);
+cudaError_t launch_xcorr_pair(int eb, const CUtensorMap* tmap_i, const CUtensorMap* tmap_j, const TcParams& prm,
+                              int max_ctas, cudaStream_t stream);
 
 // Plain CUDA-core correlator (int8 dot products into int32), the baseline.
 cudaError_t launch_xcorr_cudacore(const uint8_t* gulp, int T, int C, int N, int32_t* acc,

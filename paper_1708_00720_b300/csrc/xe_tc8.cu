@@ -1,4 +1,5 @@
-// tcgen05 X-engine, e4m3 operands: pairs of CTAs on one M = 256 MMA.
+// tcgen05 X-engine, e4m3 or float16 operands: pairs of CTAs on one M = 256
+// MMA.
 //
 // Computes, like every X-engine path here (the linear-algebra module of the
 // paper's section "Back end" applied to the 4+4-bit samples of section
@@ -26,6 +27,11 @@
 // computed as its transpose (I = j, J = nt-1) next to the last diagonal tile
 // and written back conjugated and transposed.  If the count is still odd,
 // CTA 1 repeats its partner's tile and writes nothing.
+//
+// Both operand widths share the design (template parameter EB): a stage is
+// 128 K bytes per operand row, i.e. 4 steps of 32 samples as e4m3 (one
+// K = 32 MMA per product and step) or 2 steps as float16 (u as the subnormal
+// u * 2^-24, two K = 16 MMAs per product and step).
 //
 // Per step (32 samples) of a unit:
 //  * TMA loads the raw time x input tile of I (128-byte rows, 128-byte
@@ -69,40 +75,46 @@ namespace tc8 {
 
 constexpr int kTile = 128;
 constexpr int kHalf = 64;                 // J inputs whose B rows one CTA of the pair holds
-constexpr int kStep = 32;                 // samples per MMA step (K = 32 e4m3)
-constexpr int kSteps = 4;                 // steps per pipeline stage (128 samples)
+constexpr int kStep = 32;                 // samples per step (one K = 32 e4m3 MMA, two K = 16 f16 MMAs)
 constexpr int kRawSub = kStep * kTile;    // 4096 bytes: one step of one raw tile
-constexpr int kRawTile = kSteps * kRawSub;  // 16 KB TMA box: 128 time rows x 128 inputs
-constexpr int kRawHalf = kRawTile / 2;      // 8 KB TMA box: 128 time rows x this CTA's 64 J inputs
 #ifndef XE_TC8_RAW_STAGES
 #define XE_TC8_RAW_STAGES 2
 #endif
 #ifndef XE_TC8_OP_STAGES
 #define XE_TC8_OP_STAGES 4
 #endif
-// Synchronisation happens once per stage of 4 steps: the tensor core's
-// instruction queue holds only a few MMAs, so every barrier check or commit
-// between MMAs costs issue bubbles.  Per stage the MMA thread issues 16 MMAs
-// and one commit.  A warp that issues a TMA tile load is held for roughly
-// 750 cycles per instruction, so raw tiles move in 16 KB boxes (one per
-// stage) issued by two producer warps.
+// Synchronisation happens once per stage: the tensor core's instruction
+// queue holds only a few MMAs, so every barrier check or commit between MMAs
+// costs issue bubbles.  Per stage the MMA thread issues 16 MMAs and one
+// commit: 4 steps (128 samples) of e4m3, 2 steps (64 samples) of f16, the
+// same 128 K bytes per operand row.  A warp that issues a TMA tile load is
+// held for roughly 750 cycles per instruction, so raw tiles move in one box
+// per stage and producer warp.
 constexpr int kRawStages = XE_TC8_RAW_STAGES;
 constexpr int kOpStages = XE_TC8_OP_STAGES;
-constexpr int kPlane = kHalf * kSteps * kStep;  // 8 KB: 64 rows x 128 K bytes, K-major
+constexpr int kPlane = kHalf * 128;             // 8 KB: 64 rows x 128 K bytes, K-major
 constexpr int kOpStage = 2 * kPlane;            // re plane, im plane
-constexpr int kRawStage = kRawTile + kRawHalf;  // I box (128-byte rows), half J box (64-byte rows)
 constexpr int kOpBytes = kOpStages * kOpStage;
-constexpr int kRawBytes = kRawStages * kRawStage;
 constexpr int kStageBufs = 3;                   // accumulator chunks staged per epilogue warp
 constexpr int kStageBytes = 4 * kStageBufs * 32 * 32 * 8;  // per warp and chunk: 32 rows x 32 int2
 constexpr int kSlotInts = 2 * kTile + 2 * kHalf;  // P_I, Q_I (128 each), P_J, Q_J of this CTA's half
 constexpr int kSumsBytes = 2 * kSlotInts * 4 + 2 * kTile * 4 + 2 * kTile * 4;
 // 2 slots of sums, column corrections (re, im), row and column triangle offsets
-constexpr int kBarOffset = kOpBytes + kRawBytes + kStageBytes + kSumsBytes;
 constexpr int kNumBars = 2 * kRawStages + 2 * kOpStages + 2 + 2 + 2 + 1;
-constexpr int kSmemBytes = kBarOffset + kNumBars * 8 + 16 + 1024;
-static_assert(kSmemBytes <= 227 * 1024, "shared memory budget");
-static_assert(kOpBytes % 1024 == 0 && kRawBytes % 1024 == 0, "swizzled tiles need 1024-byte alignment");
+
+// Operand width EB (1: e4m3, 2: f16) sets the samples per stage and the raw tiles.
+template <int EB>
+struct Geo {
+  static constexpr int kSteps = EB == 1 ? 4 : 2;        // 32-sample steps per stage
+  static constexpr int kRawTile = kSteps * kRawSub;     // TMA box: stage rows x 128 inputs
+  static constexpr int kRawHalf = kRawTile / 2;         // TMA box: stage rows x this CTA's 64 J inputs
+  static constexpr int kRawStage = kRawTile + kRawHalf; // I box (128-byte rows), half J box (64-byte rows)
+  static constexpr int kRawBytes = kRawStages * kRawStage;
+  static constexpr int kBarOffset = kOpBytes + kRawBytes + kStageBytes + kSumsBytes;
+  static constexpr int kSmemBytes = kBarOffset + kNumBars * 8 + 16 + 1024;
+  static_assert(kSmemBytes <= 227 * 1024, "shared memory budget");
+  static_assert(kOpBytes % 1024 == 0 && kRawStage % 1024 == 0, "swizzled tiles need 1024-byte alignment");
+};
 
 // Warp roles.  Warp w issues from SM sub-partition w % 4; the A-side and
 // epilogue warps need their warp index = TMEM lane quadrant (mod 4).
@@ -116,8 +128,8 @@ constexpr int kAWarps = 8;
 constexpr int kBWarps = 4;
 constexpr int kStageArrivals = kAWarps + kBWarps;   // per CTA and stage
 constexpr int kTmemCols = 512;
-constexpr int kTmemA0 = 256;              // A stages: 64 columns each (4 steps x (re 8 + im 8))
-constexpr int kTmemAStage = 16 * kSteps;
+constexpr int kTmemA0 = 256;              // A stages: 64 columns each (128 K bytes of re and of im)
+constexpr int kTmemAStage = 64;
 static_assert(kTmemA0 + kTmemAStage * kOpStages <= kTmemCols, "tensor memory budget");
 
 __device__ __forceinline__ bool is_a_warp(int w) { return (w >= 4 && w < 8) || (w >= 12 && w < 16); }
@@ -133,7 +145,7 @@ enum ErrCode : int {
 
 struct Smem {
   uint8_t* op;     // [kOpStages][re, im][64 rows x 128 K bytes]  B planes (this CTA's half)
-  uint8_t* raw;    // [kRawStages][I: kRawTile | J half: kRawHalf]
+  uint8_t* raw;    // [kRawStages][I: kRawTile | J half: kRawHalf]  (Geo<EB>)
   int2* stage;     // [4 warps][kStageBufs][32 rows][32], column index XOR row
   int* sums;       // [2][kSlotInts]
   float* colcorr;  // [2][128]: per-column bias corrections of the current unit (re, im)
@@ -145,16 +157,18 @@ struct Smem {
   int* abort_flag;
 };
 
+template <int EB>
 __device__ __forceinline__ Smem carve(uint8_t* base) {
+  using G = Geo<EB>;
   Smem p;
   p.op = base;
   p.raw = base + kOpBytes;
-  p.stage = reinterpret_cast<int2*>(base + kOpBytes + kRawBytes);
-  p.sums = reinterpret_cast<int*>(base + kOpBytes + kRawBytes + kStageBytes);
+  p.stage = reinterpret_cast<int2*>(base + kOpBytes + G::kRawBytes);
+  p.sums = reinterpret_cast<int*>(base + kOpBytes + G::kRawBytes + kStageBytes);
   p.colcorr = reinterpret_cast<float*>(p.sums + 2 * kSlotInts);
   p.rowoff = reinterpret_cast<int*>(p.colcorr + 2 * kTile);
   p.coloff = p.rowoff + kTile;
-  uint64_t* b = reinterpret_cast<uint64_t*>(base + kBarOffset);
+  uint64_t* b = reinterpret_cast<uint64_t*>(base + G::kBarOffset);
   p.raw_full = b; b += kRawStages;
   p.raw_empty = b; b += kRawStages;
   p.op_full = b; b += kOpStages;
@@ -232,6 +246,12 @@ __device__ __forceinline__ void mma2_f8_tmem_a(uint32_t d_tmem, uint32_t a_tmem,
                                                uint32_t idesc, uint32_t accumulate) {
   asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
                "tcgen05.mma.cta_group::2.kind::f8f6f4 [%0], [%1], %2, %3, p;\n\t}"
+               ::"r"(d_tmem), "r"(a_tmem), "l"(b_desc), "r"(idesc), "r"(accumulate));
+}
+__device__ __forceinline__ void mma2_f16_tmem_a(uint32_t d_tmem, uint32_t a_tmem, uint64_t b_desc,
+                                                uint32_t idesc, uint32_t accumulate) {
+  asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+               "tcgen05.mma.cta_group::2.kind::f16 [%0], [%1], %2, %3, p;\n\t}"
                ::"r"(d_tmem), "r"(a_tmem), "l"(b_desc), "r"(idesc), "r"(accumulate));
 }
 // Completion of this thread's earlier MMAs arrives on `bar` in both CTAs.
@@ -313,6 +333,14 @@ __device__ __forceinline__ void tmem_st_16x256b_x2(uint32_t taddr, uint32_t r0, 
                ::"r"(taddr), "r"(r0), "r"(r1), "r"(r2), "r"(r3), "r"(r4), "r"(r5), "r"(r6), "r"(r7)
                : "memory");
 }
+// .x4: the re plane (16 columns = 32 float16 of K) and the im plane of one step
+__device__ __forceinline__ void tmem_st_16x256b_x4(uint32_t taddr, const uint32_t (&r)[16]) {
+  asm volatile("tcgen05.st.sync.aligned.16x256b.x4.b32 [%0], "
+               "{%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,%16};"
+               ::"r"(taddr), "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]),
+                 "r"(r[8]), "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15])
+               : "memory");
+}
 __device__ __forceinline__ void tmem_st_wait() {
   asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
 }
@@ -354,6 +382,11 @@ __device__ __forceinline__ Words unpack_words(const uint32_t (&d)[4], uint32_t (
   return o;
 }
 
+// Four biased bytes -> two words of two float16 bit patterns each (u as the
+// subnormal u * 2^-24): (b0, b1) and (b2, b3).
+__device__ __forceinline__ uint32_t f16_lo(uint32_t w) { return __byte_perm(w, 0u, 0x4140); }
+__device__ __forceinline__ uint32_t f16_hi(uint32_t w) { return __byte_perm(w, 0u, 0x4342); }
+
 // Per-lane sums of the biased parts of inputs 2p + e: byte lanes (at most
 // 4 x 30 per stage) folded into ints every second stage.
 struct PairSums {
@@ -387,8 +420,11 @@ struct PairSums {
 // staging buffer (row `lane`, column index XOR lane).  Every correction is a
 // multiple of 8 below 2^27 and the corrected value an integer below 2^23, so
 // one FFMA per value is exact.
+// D holds sums of products of u * 2^-9 (e4m3) or u * 2^-24 (f16) values.
+template <int EB>
 __device__ __forceinline__ void stage_chunk(int2* buf, const uint32_t (&vre)[32], const uint32_t (&vim)[32],
                                             const float* colcorr, float row_re, float row_im, int lane) {
+  constexpr float kScale = EB == 1 ? 262144.0f : 281474976710656.0f;   // 2^18, 2^48
   const float4* cre4 = reinterpret_cast<const float4*>(colcorr);
   const float4* cim4 = reinterpret_cast<const float4*>(colcorr + kTile);
 #pragma unroll
@@ -398,19 +434,21 @@ __device__ __forceinline__ void stage_chunk(int2* buf, const uint32_t (&vre)[32]
 #pragma unroll
     for (int e = 0; e < 4; ++e) {
       const int k = 4 * k4 + e;
-      const int re = __float2int_rn(__fmaf_rn(__uint_as_float(vre[k]), 262144.0f, row_re + crv[e]));
-      const int im = __float2int_rn(__fmaf_rn(__uint_as_float(vim[k]), 262144.0f, row_im + civ[e]));
+      const int re = __float2int_rn(__fmaf_rn(__uint_as_float(vre[k]), kScale, row_re + crv[e]));
+      const int im = __float2int_rn(__fmaf_rn(__uint_as_float(vim[k]), kScale, row_im + civ[e]));
       buf[lane * 32 + (k ^ lane)] = make_int2(re, im);
     }
   }
 }
 
+template <int EB>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
 xcorr_tc8_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CUtensorMap tmap_j, TcParams prm) {
+  using G = Geo<EB>;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
                                              ~static_cast<uintptr_t>(1023));
-  const Smem s = carve(base);
+  const Smem s = carve<EB>(base);
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const uint32_t rank = cluster_rank();
   const uint32_t peer = rank ^ 1u;
@@ -464,19 +502,19 @@ xcorr_tc8_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant
       for (int u = cl; u < prm.units && ok; u += ncl) {
         const Unit t = decode_unit(u, per_chan, nt, rank);
         const bool own_diag = (t.ti == t.tj);
-        for (int ks = 0; ks < nks; ks += kSteps, ++rit) {
+        for (int ks = 0; ks < nks; ks += G::kSteps, ++rit) {
           const int st = rit % kRawStages;
           if (!wait_or_abort(&s.raw_empty[st], ((rit / kRawStages) & 1) ^ 1, lim, abort_flag)) {
             fail(s, prm.err, kErrWaitRawEmpty);
             ok = false;
             break;
           }
-          uint8_t* dst = s.raw + st * kRawStage + tile * kRawTile;
+          uint8_t* dst = s.raw + st * G::kRawStage + tile * G::kRawTile;
           if (tile == 0) {
-            mbar_arrive_expect_tx(&s.raw_full[st], kRawTile);
+            mbar_arrive_expect_tx(&s.raw_full[st], G::kRawTile);
             tma_load_3d(dst, &tmap, &s.raw_full[st], t.ti * kTile, t.c, ks * kStep);
           } else if (!own_diag) {
-            mbar_arrive_expect_tx(&s.raw_full[st], kRawHalf);
+            mbar_arrive_expect_tx(&s.raw_full[st], G::kRawHalf);
             tma_load_3d(dst, &tmap_j, &s.raw_full[st], t.tj * kTile + kHalf * static_cast<int>(rank), t.c,
                         ks * kStep);
           } else {
@@ -497,7 +535,7 @@ xcorr_tc8_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant
       int sit = 0;
       bool ok = true;
       for (int u = cl; u < prm.units && ok; u += ncl) {
-        for (int ks = 0; ks < nks; ks += kSteps, ++sit) {
+        for (int ks = 0; ks < nks; ks += G::kSteps, ++sit) {
           const int st = sit % kOpStages;
           if (!wait_or_abort(&s.op_full[st], (sit / kOpStages) & 1, lim, abort_flag)) {
             fail(s, prm.err, kErrWaitOpFull);
@@ -513,7 +551,7 @@ xcorr_tc8_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant
     if (lane == 0) {
       int sit = 0, ui = 0;
       bool ok = true;
-      // A from tensor memory, B K-major; e4m3 x e4m3 -> f32, M = 256 (pair), N = 128
+      // A from tensor memory, B K-major; e4m3 x e4m3 or f16 x f16 -> f32, M = 256 (pair), N = 128
       constexpr uint32_t id_pos = (1u << 4) | ((128u >> 3) << 17) | ((256u >> 4) << 24);
       constexpr uint32_t id_neg = id_pos | (1u << 14);
       const uint32_t d_re = tmem, d_im = tmem + 128;
@@ -523,7 +561,7 @@ xcorr_tc8_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant
           break;
         }
         tc_fence_after();
-        for (int ks = 0; ks < nks; ks += kSteps, ++sit) {
+        for (int ks = 0; ks < nks; ks += G::kSteps, ++sit) {
           const int st = sit % kOpStages;
           if (!wait_or_abort(&s.op_full[st], (sit / kOpStages) & 1, lim, abort_flag)) {
             fail(s, prm.err, kErrWaitOpFull);
@@ -533,16 +571,35 @@ xcorr_tc8_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant
           tc_fence_after();
           const uint32_t a0 = tmem + kTmemA0 + kTmemAStage * st;
           const uint32_t op = smem_u32(s.op + st * kOpStage);
+          if constexpr (EB == 1) {
+            // per step: A columns re 8 | im 8, B K bytes 32
 #pragma unroll
-          for (int sub = 0; sub < kSteps; ++sub) {
-            const uint32_t a_re = a0 + 16 * sub, a_im = a_re + 8;
-            const uint64_t b_re = sdesc_k_sw128(op + 32 * sub);
-            const uint64_t b_im = sdesc_k_sw128(op + kPlane + 32 * sub);
-            const uint32_t acc0 = (ks + sub) > 0 ? 1u : 0u;
-            mma2_f8_tmem_a(d_re, a_re, b_re, id_pos, acc0);
-            mma2_f8_tmem_a(d_re, a_im, b_im, id_pos, 1u);
-            mma2_f8_tmem_a(d_im, a_im, b_re, id_pos, acc0);
-            mma2_f8_tmem_a(d_im, a_re, b_im, id_neg, 1u);
+            for (int sub = 0; sub < G::kSteps; ++sub) {
+              const uint32_t a_re = a0 + 16 * sub, a_im = a_re + 8;
+              const uint64_t b_re = sdesc_k_sw128(op + 32 * sub);
+              const uint64_t b_im = sdesc_k_sw128(op + kPlane + 32 * sub);
+              const uint32_t acc0 = (ks + sub) > 0 ? 1u : 0u;
+              mma2_f8_tmem_a(d_re, a_re, b_re, id_pos, acc0);
+              mma2_f8_tmem_a(d_re, a_im, b_im, id_pos, 1u);
+              mma2_f8_tmem_a(d_im, a_im, b_re, id_pos, acc0);
+              mma2_f8_tmem_a(d_im, a_re, b_im, id_neg, 1u);
+            }
+          } else {
+            // per step: A columns re 16 | im 16 (two K = 16 halves of 8 each),
+            // B K bytes 64 (two halves of 32)
+#pragma unroll
+            for (int sub = 0; sub < G::kSteps; ++sub)
+#pragma unroll
+              for (int kk = 0; kk < 2; ++kk) {
+                const uint32_t a_re = a0 + 32 * sub + 8 * kk, a_im = a_re + 16;
+                const uint64_t b_re = sdesc_k_sw128(op + 64 * sub + 32 * kk);
+                const uint64_t b_im = sdesc_k_sw128(op + kPlane + 64 * sub + 32 * kk);
+                const uint32_t acc0 = (ks + sub + kk) > 0 ? 1u : 0u;
+                mma2_f16_tmem_a(d_re, a_re, b_re, id_pos, acc0);
+                mma2_f16_tmem_a(d_re, a_im, b_im, id_pos, 1u);
+                mma2_f16_tmem_a(d_im, a_im, b_re, id_pos, acc0);
+                mma2_f16_tmem_a(d_im, a_re, b_im, id_neg, 1u);
+              }
           }
           commit2(&s.op_empty[st]);
         }
@@ -564,7 +621,7 @@ xcorr_tc8_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant
       PairSums ps;
       ps.zero();
       int since_fold = 0;
-      for (int ks = 0; ks < nks; ks += kSteps, ++sit) {
+      for (int ks = 0; ks < nks; ks += G::kSteps, ++sit) {
         const int rst = sit % kRawStages, ost = sit % kOpStages;
         if (!wait_or_abort(&s.raw_full[rst], (sit / kRawStages) & 1, lim, abort_flag)) {
           fail(s, prm.err, kErrWaitRawFull);
@@ -573,10 +630,10 @@ xcorr_tc8_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant
         }
         // the four transposing loads first (their latencies overlap), while
         // the MMA may still hold the operand stage
-        const uint32_t rawI_s = smem_u32(s.raw + rst * kRawStage);
-        uint32_t dv[kSteps][4];
+        const uint32_t rawI_s = smem_u32(s.raw + rst * G::kRawStage);
+        uint32_t dv[G::kSteps][4];
 #pragma unroll
-        for (int sub = 0; sub < kSteps; ++sub)
+        for (int sub = 0; sub < G::kSteps; ++sub)
           ldsm_x4_trans(rawI_s + sub * kRawSub + sw128(lane, ch), dv[sub][0], dv[sub][1], dv[sub][2], dv[sub][3]);
         if (!wait_or_abort(&s.op_empty[ost], ((sit / kOpStages) & 1) ^ 1, lim, abort_flag)) {
           fail(s, prm.err, kErrWaitOpEmpty);
@@ -585,9 +642,19 @@ xcorr_tc8_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant
         }
         const uint32_t ta0 = tmem + kTmemA0 + kTmemAStage * ost + lane_off;
 #pragma unroll
-        for (int sub = 0; sub < kSteps; ++sub) {
+        for (int sub = 0; sub < G::kSteps; ++sub) {
           const Words w = unpack_words(dv[sub], ps.bP, ps.bQ);
-          tmem_st_16x256b_x2(ta0 + 16 * sub, w.re0, w.re1, w.re2, w.re3, w.im0, w.im1, w.im2, w.im3);
+          if constexpr (EB == 1) {
+            tmem_st_16x256b_x2(ta0 + 16 * sub, w.re0, w.re1, w.re2, w.re3, w.im0, w.im1, w.im2, w.im3);
+          } else {
+            // float16: re K 0-15 | re K 16-31 | im K 0-15 | im K 16-31, 8 columns each;
+            // a thread's first four samples go to the first K half, the next four to the second
+            const uint32_t r[16] = {f16_lo(w.re0), f16_hi(w.re0), f16_lo(w.re2), f16_hi(w.re2),
+                                    f16_lo(w.re1), f16_hi(w.re1), f16_lo(w.re3), f16_hi(w.re3),
+                                    f16_lo(w.im0), f16_hi(w.im0), f16_lo(w.im2), f16_hi(w.im2),
+                                    f16_lo(w.im1), f16_hi(w.im1), f16_lo(w.im3), f16_hi(w.im3)};
+            tmem_st_16x256b_x4(ta0 + 32 * sub, r);
+          }
         }
         tmem_st_wait();
         tc_fence_before();
@@ -596,7 +663,7 @@ xcorr_tc8_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant
           mbar_arrive(&s.op_full[ost]);
           mbar_arrive(&s.raw_empty[rst]);
         }
-        if (++since_fold == 2 || ks + kSteps >= nks) {
+        if (++since_fold == 2 || ks + G::kSteps >= nks) {
           ps.fold();
           since_fold = 0;
         }
@@ -635,7 +702,7 @@ xcorr_tc8_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant
       PairSums ps;
       ps.zero();
       int since_fold = 0;
-      for (int ks = 0; ks < nks; ks += kSteps, ++sit) {
+      for (int ks = 0; ks < nks; ks += G::kSteps, ++sit) {
         const int rst = sit % kRawStages, ost = sit % kOpStages;
         if (!wait_or_abort(&s.raw_full[rst], (sit / kRawStages) & 1, lim, abort_flag)) {
           fail(s, prm.err, kErrWaitRawFull);
@@ -644,13 +711,13 @@ xcorr_tc8_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant
         }
         // this CTA's 64 J inputs: 64-byte rows of the half tile (chunk g at
         // g XOR ((t >> 1) & 3) in row t), or chunk q of the I tile when I == J
-        const uint32_t raw_s = smem_u32(s.raw + rst * kRawStage);
+        const uint32_t raw_s = smem_u32(s.raw + rst * G::kRawStage);
         const uint32_t rowJ = own_diag ? raw_s + sw128(lane, q)
-                                       : raw_s + kRawTile + lane * 64 + ((g ^ ((lane >> 1) & 3)) << 4);
+                                       : raw_s + G::kRawTile + lane * 64 + ((g ^ ((lane >> 1) & 3)) << 4);
         const uint32_t subJ = own_diag ? kRawSub : kRawSub / 2;
-        uint32_t dv[kSteps][4];
+        uint32_t dv[G::kSteps][4];
 #pragma unroll
-        for (int sub = 0; sub < kSteps; ++sub)
+        for (int sub = 0; sub < G::kSteps; ++sub)
           ldsm_x4_trans(rowJ + sub * subJ, dv[sub][0], dv[sub][1], dv[sub][2], dv[sub][3]);
         if (!wait_or_abort(&s.op_empty[ost], ((sit / kOpStages) & 1) ^ 1, lim, abort_flag)) {
           fail(s, prm.err, kErrWaitOpEmpty);
@@ -659,15 +726,30 @@ xcorr_tc8_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant
         }
         const uint32_t opB = smem_u32(s.op + ost * kOpStage);
 #pragma unroll
-        for (int sub = 0; sub < kSteps; ++sub) {
+        for (int sub = 0; sub < G::kSteps; ++sub) {
           const Words w = unpack_words(dv[sub], ps.bP, ps.bQ);
-          // K-major rows n0 and n0 + 8 (same swizzle phase), K bytes 32 sub + 8 kq
-          const int kb = 32 * sub + 8 * kq;
-          const uint32_t off = static_cast<uint32_t>(n0 * 128 + (((kb >> 4) ^ (n0 & 7)) << 4) + (kb & 15));
-          sts64(opB + off, w.re0, w.re1);
-          sts64(opB + off + 8 * 128, w.re2, w.re3);
-          sts64(opB + kPlane + off, w.im0, w.im1);
-          sts64(opB + kPlane + off + 8 * 128, w.im2, w.im3);
+          // K-major rows n0 and n0 + 8 (same swizzle phase), the same K
+          // positions as the A side
+          if constexpr (EB == 1) {
+            const int kb = 32 * sub + 8 * kq;
+            const uint32_t off = static_cast<uint32_t>(n0 * 128 + (((kb >> 4) ^ (n0 & 7)) << 4) + (kb & 15));
+            sts64(opB + off, w.re0, w.re1);
+            sts64(opB + off + 8 * 128, w.re2, w.re3);
+            sts64(opB + kPlane + off, w.im0, w.im1);
+            sts64(opB + kPlane + off + 8 * 128, w.im2, w.im3);
+          } else {
+            const int kb0 = 64 * sub + 8 * kq, kb1 = kb0 + 32;
+            const uint32_t o0 = static_cast<uint32_t>(n0 * 128 + (((kb0 >> 4) ^ (n0 & 7)) << 4) + (kb0 & 15));
+            const uint32_t o1 = static_cast<uint32_t>(n0 * 128 + (((kb1 >> 4) ^ (n0 & 7)) << 4) + (kb1 & 15));
+            sts64(opB + o0, f16_lo(w.re0), f16_hi(w.re0));
+            sts64(opB + o1, f16_lo(w.re1), f16_hi(w.re1));
+            sts64(opB + o0 + 8 * 128, f16_lo(w.re2), f16_hi(w.re2));
+            sts64(opB + o1 + 8 * 128, f16_lo(w.re3), f16_hi(w.re3));
+            sts64(opB + kPlane + o0, f16_lo(w.im0), f16_hi(w.im0));
+            sts64(opB + kPlane + o1, f16_lo(w.im1), f16_hi(w.im1));
+            sts64(opB + kPlane + o0 + 8 * 128, f16_lo(w.im2), f16_hi(w.im2));
+            sts64(opB + kPlane + o1 + 8 * 128, f16_lo(w.im3), f16_hi(w.im3));
+          }
         }
         fence_proxy_async_smem();
         __syncwarp();
@@ -675,7 +757,7 @@ xcorr_tc8_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant
           mbar_arrive(&s.op_full[ost]);
           mbar_arrive(&s.raw_empty[rst]);
         }
-        if (++since_fold == 2 || ks + kSteps >= nks) {
+        if (++since_fold == 2 || ks + G::kSteps >= nks) {
           ps.fold();
           since_fold = 0;
         }
@@ -773,7 +855,7 @@ xcorr_tc8_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant
           tmem_ld32(t_row + cc, vre);
           tmem_ld32(t_row + 128 + cc, vim);
           tmem_ld_wait();
-          if (cc < kStageBufs * 32) stage_chunk(stg + (cc >> 5) * 1024, vre, vim, s.colcorr + cc, row_re, row_im, lane);
+          if (cc < kStageBufs * 32) stage_chunk<EB>(stg + (cc >> 5) * 1024, vre, vim, s.colcorr + cc, row_re, row_im, lane);
         }
         tc_fence_before();
         __syncwarp();
@@ -785,7 +867,7 @@ xcorr_tc8_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant
           const int2* sb = stg + (b == 3 ? 0 : b) * 1024;
           if (b == 3) {  // buffer 0 has been written out: chunk 3 goes there
             __syncwarp();
-            stage_chunk(stg, vre, vim, s.colcorr + cc, row_re, row_im, lane);
+            stage_chunk<EB>(stg, vre, vim, s.colcorr + cc, row_re, row_im, lane);
           }
           __syncwarp();
           if (!t.transposed) {
@@ -869,12 +951,14 @@ xcorr_tc8_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant
 
 }  // namespace tc8
 
-int tc8_smem_bytes() { return tc8::kSmemBytes; }
+int tc8_smem_bytes(int eb) { return eb == 1 ? tc8::Geo<1>::kSmemBytes : tc8::Geo<2>::kSmemBytes; }
 
-cudaError_t launch_xcorr_tc8(const CUtensorMap* tmap_i, const CUtensorMap* tmap_j, TcParams prm, int max_ctas,
-                             cudaStream_t stream) {
-  cudaError_t e = cudaFuncSetAttribute(tc8::xcorr_tc8_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       tc8::kSmemBytes);
+namespace {
+template <int EB>
+cudaError_t launch_pair(const CUtensorMap* tmap_i, const CUtensorMap* tmap_j, TcParams prm, int max_ctas,
+                        cudaStream_t stream) {
+  constexpr int smem = tc8::Geo<EB>::kSmemBytes;
+  cudaError_t e = cudaFuncSetAttribute(tc8::xcorr_tc8_kernel<EB>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
   // clusters that can be resident at once (pairs of SMs), asked once per process
   static int resident_clusters = -1;
@@ -882,9 +966,9 @@ cudaError_t launch_xcorr_tc8(const CUtensorMap* tmap_i, const CUtensorMap* tmap_
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(2, 1, 1);
     cfg.blockDim = dim3(tc8::kThreads, 1, 1);
-    cfg.dynamicSmemBytes = tc8::kSmemBytes;
+    cfg.dynamicSmemBytes = smem;
     int n = 0;
-    if (cudaOccupancyMaxActiveClusters(&n, tc8::xcorr_tc8_kernel, &cfg) != cudaSuccess || n < 1) {
+    if (cudaOccupancyMaxActiveClusters(&n, tc8::xcorr_tc8_kernel<EB>, &cfg) != cudaSuccess || n < 1) {
       cudaGetLastError();
       n = 0;
     }
@@ -897,9 +981,15 @@ cudaError_t launch_xcorr_tc8(const CUtensorMap* tmap_i, const CUtensorMap* tmap_
   if (resident_clusters > 0 && resident_clusters < clusters) clusters = resident_clusters;
   if (units < clusters) clusters = units;
   if (clusters < 1) clusters = 1;
-  tc8::xcorr_tc8_kernel<<<static_cast<int>(2 * clusters), tc8::kThreads, tc8::kSmemBytes, stream>>>(*tmap_i, *tmap_j,
-                                                                                                  prm);
+  tc8::xcorr_tc8_kernel<EB><<<static_cast<int>(2 * clusters), tc8::kThreads, smem, stream>>>(*tmap_i, *tmap_j, prm);
   return cudaGetLastError();
+}
+}  // namespace
+
+cudaError_t launch_xcorr_pair(int eb, const CUtensorMap* tmap_i, const CUtensorMap* tmap_j, const TcParams& prm,
+                              int max_ctas, cudaStream_t stream) {
+  return eb == 1 ? launch_pair<1>(tmap_i, tmap_j, prm, max_ctas, stream)
+                 : launch_pair<2>(tmap_i, tmap_j, prm, max_ctas, stream);
 }
 
 }  // namespace xe
