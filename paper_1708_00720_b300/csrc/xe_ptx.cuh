@@ -83,13 +83,6 @@ __device__ __forceinline__ void tma_load_3d(void* smem_dst, const void* desc, ui
       : "memory");
 }
 
-// L2 prefetch of one tile of a 3-D tensor (no shared-memory destination).
-__device__ __forceinline__ void tma_prefetch_3d(const void* desc, int x, int y, int z) {
-  asm volatile("cp.async.bulk.prefetch.tensor.3d.L2.global.tile [%0, {%1, %2, %3}];"
-               ::"l"(reinterpret_cast<uint64_t>(desc)), "r"(x), "r"(y), "r"(z)
-               : "memory");
-}
-
 // ------------------------------------------------------------------ tcgen05
 template <int NCOLS>
 __device__ __forceinline__ void tmem_alloc(uint32_t* slot_smem) {
@@ -108,41 +101,6 @@ __device__ __forceinline__ void tc_fence_before() {
 }
 __device__ __forceinline__ void tc_fence_after() {
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-}
-
-// Shared-memory matrix descriptor, MN-major operand, 128-byte swizzle.
-//   lbo: byte distance between 128-byte-wide column blocks along M/N
-//   sbo: byte distance between groups of 8 rows along K
-__device__ __forceinline__ uint64_t sdesc_mn_sw128(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
-  uint64_t d = 0;
-  d |= static_cast<uint64_t>((saddr >> 4) & 0x3FFFu);
-  d |= static_cast<uint64_t>((lbo >> 4) & 0x3FFFu) << 16;
-  d |= static_cast<uint64_t>((sbo >> 4) & 0x3FFFu) << 32;
-  d |= 1ull << 46;  // descriptor version for tcgen05
-  d |= 2ull << 61;  // SWIZZLE_128B
-  return d;
-}
-
-// Instruction descriptor: dense, D = f32, A/B format codes, both operands
-// MN-major, optional negation of B.
-//   kind::f8f6f4: fmt 0 = e4m3;  kind::f16: fmt 0 = f16
-__host__ __device__ constexpr uint32_t idesc_mn(int M, int N, uint32_t fmt, bool negB) {
-  return (1u << 4) | (fmt << 7) | (fmt << 10) | ((negB ? 1u : 0u) << 14) | (1u << 15) | (1u << 16) |
-         (static_cast<uint32_t>(N >> 3) << 17) | (static_cast<uint32_t>(M >> 4) << 24);
-}
-
-__device__ __forceinline__ void mma_f8f6f4(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc,
-                                           uint32_t idesc, uint32_t accumulate) {
-  asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-               "tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n\t}"
-               ::"r"(d_tmem), "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate));
-}
-
-__device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t a_desc, uint64_t b_desc,
-                                        uint32_t idesc, uint32_t accumulate) {
-  asm volatile("{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-               "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}"
-               ::"r"(d_tmem), "l"(a_desc), "l"(b_desc), "r"(idesc), "r"(accumulate));
 }
 
 // Make the mbarrier track completion of all previously issued MMAs of this thread.
