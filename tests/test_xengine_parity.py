@@ -52,6 +52,12 @@ SMALL_SHAPES = [  # (N, C, T): tile-ragged inputs, time tails, single samples
     (256, 5, 64),
     (16, 1, 31),
     (400, 1, 96),
+    # 128-input tiles per side nt = 5, 6, 7: the tensor-core paths group tile
+    # pairs by J column two at a time, compute a column's odd one out as its
+    # transpose and, for an odd total (nt = 5, 6), repeat one tile unwritten
+    (640, 1, 40),
+    (736, 2, 33),
+    (896, 1, 64),
 ]
 
 
