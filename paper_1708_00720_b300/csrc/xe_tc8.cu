@@ -416,29 +416,23 @@ struct PairSums {
   }
 };
 
-// Bias removal of one 32-column chunk of this lane's accumulator row into a
-// staging buffer (row `lane`, column index XOR lane).  Every correction is a
-// multiple of 8 below 2^27 and the corrected value an integer below 2^23, so
-// one FFMA per value is exact.
-// D holds sums of products of u * 2^-9 (e4m3) or u * 2^-24 (f16) values.
+// One 32-column chunk of this lane's accumulator row, as raw float32 bits,
+// into a staging buffer (row `lane`, column index XOR lane): the quickest way
+// to get D out of tensor memory.  The bias is removed after D is released.
+__device__ __forceinline__ void stage_raw(int2* buf, const uint32_t (&vre)[32], const uint32_t (&vim)[32], int lane) {
+#pragma unroll
+  for (int k = 0; k < 32; ++k) buf[lane * 32 + (k ^ lane)] = make_int2(static_cast<int>(vre[k]), static_cast<int>(vim[k]));
+}
+
+// Bias removal of one staged value: D holds sums of products of u * 2^-9
+// (e4m3) or u * 2^-24 (f16) values; every correction is a multiple of 8
+// below 2^27 and the corrected value an integer below 2^23, so one FFMA per
+// value is exact.
 template <int EB>
-__device__ __forceinline__ void stage_chunk(int2* buf, const uint32_t (&vre)[32], const uint32_t (&vim)[32],
-                                            const float* colcorr, float row_re, float row_im, int lane) {
+__device__ __forceinline__ int2 unbias(int2 raw, float rre, float rim, float cre, float cim) {
   constexpr float kScale = EB == 1 ? 262144.0f : 281474976710656.0f;   // 2^18, 2^48
-  const float4* cre4 = reinterpret_cast<const float4*>(colcorr);
-  const float4* cim4 = reinterpret_cast<const float4*>(colcorr + kTile);
-#pragma unroll
-  for (int k4 = 0; k4 < 8; ++k4) {
-    const float4 cr = cre4[k4], ci = cim4[k4];
-    const float crv[4] = {cr.x, cr.y, cr.z, cr.w}, civ[4] = {ci.x, ci.y, ci.z, ci.w};
-#pragma unroll
-    for (int e = 0; e < 4; ++e) {
-      const int k = 4 * k4 + e;
-      const int re = __float2int_rn(__fmaf_rn(__uint_as_float(vre[k]), kScale, row_re + crv[e]));
-      const int im = __float2int_rn(__fmaf_rn(__uint_as_float(vim[k]), kScale, row_im + civ[e]));
-      buf[lane * 32 + (k ^ lane)] = make_int2(re, im);
-    }
-  }
+  return make_int2(__float2int_rn(__fmaf_rn(__int_as_float(raw.x), kScale, rre + cre)),
+                   __float2int_rn(__fmaf_rn(__int_as_float(raw.y), kScale, rim + cim)));
 }
 
 template <int EB>
@@ -807,7 +801,7 @@ xcorr_tc8_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant
       const int* sl = s.sums + slot * kSlotInts;
       float row_re = 0.f, row_im = 0.f;
       if (ok) {
-        // bias corrections of this lane's row and of column L (see stage_chunk)
+        // bias corrections of this lane's row and of column L (see unbias)
         row_re = static_cast<float>(-8 * (sl[il] + sl[kTile + il]) + 128 * T_pad);
         row_im = static_cast<float>(8 * (sl[il] - sl[kTile + il]));
         // column L is J input il; its half (L / 64) is held by CTA L / 64
@@ -846,16 +840,17 @@ xcorr_tc8_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant
         const bool tfull = t.transposed && t.tj * kTile + kTile <= prm.N;
         const int gI = t.ti * kTile + il;           // this lane's row input
         const int* ro = s.rowoff + 32 * quad;
-        // D leaves tensor memory first: chunks 0-2 (32 columns each) corrected
-        // into shared staging, chunk 3 into registers; then D is released and
-        // the global writes run while the MMA works on the next unit.
+        // D leaves tensor memory first: chunks 0-2 (32 columns each) as raw
+        // bits into shared staging, chunk 3 into registers; then D is released
+        // and the bias removal and global writes run while the MMA works on the
+        // next unit.
         uint32_t vre[32], vim[32];
 #pragma unroll 1
         for (int cc = 0; cc < kTile; cc += 32) {
           tmem_ld32(t_row + cc, vre);
           tmem_ld32(t_row + 128 + cc, vim);
           tmem_ld_wait();
-          if (cc < kStageBufs * 32) stage_chunk<EB>(stg + (cc >> 5) * 1024, vre, vim, s.colcorr + cc, row_re, row_im, lane);
+          if (cc < kStageBufs * 32) stage_raw(stg + (cc >> 5) * 1024, vre, vim, lane);
         }
         tc_fence_before();
         __syncwarp();
@@ -867,20 +862,26 @@ xcorr_tc8_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant
           const int2* sb = stg + (b == 3 ? 0 : b) * 1024;
           if (b == 3) {  // buffer 0 has been written out: chunk 3 goes there
             __syncwarp();
-            stage_chunk<EB>(stg, vre, vim, s.colcorr + cc, row_re, row_im, lane);
+            stage_raw(stg, vre, vim, lane);
           }
           __syncwarp();
           if (!t.transposed) {
-            // 32 rows x 32 baselines: each row is 256 contiguous bytes (lanes permuted)
+            // 32 rows x 32 baselines: each row is 256 contiguous bytes (lanes
+            // permuted); row r's corrections come from lane r
             const int gj = t.tj * kTile + lane_to_input(cc + lane);
+            const float cre = s.colcorr[cc + lane], cim = s.colcorr[kTile + cc + lane];
             int2* accj = acc + gj;
             if (full && !prm.accumulate) {
 #pragma unroll 4
-              for (int r = 0; r < 32; ++r) accj[ro[r]] = sb[r * 32 + (lane ^ r)];
+              for (int r = 0; r < 32; ++r) {
+                const float rre = __shfl_sync(0xFFFFFFFFu, row_re, r), rim = __shfl_sync(0xFFFFFFFFu, row_im, r);
+                accj[ro[r]] = unbias<EB>(sb[r * 32 + (lane ^ r)], rre, rim, cre, cim);
+              }
             } else if (full) {
 #pragma unroll 4
               for (int r = 0; r < 32; ++r) {
-                const int2 v = sb[r * 32 + (lane ^ r)];
+                const float rre = __shfl_sync(0xFFFFFFFFu, row_re, r), rim = __shfl_sync(0xFFFFFFFFu, row_im, r);
+                const int2 v = unbias<EB>(sb[r * 32 + (lane ^ r)], rre, rim, cre, cim);
                 int2* dst = accj + ro[r];
                 const int2 o = *dst;
                 *dst = make_int2(o.x + v.x, o.y + v.y);
@@ -888,9 +889,10 @@ xcorr_tc8_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant
             } else {
 #pragma unroll 4
               for (int r = 0; r < 32; ++r) {
+                const float rre = __shfl_sync(0xFFFFFFFFu, row_re, r), rim = __shfl_sync(0xFFFFFFFFu, row_im, r);
                 const int gi = t.ti * kTile + lane_to_input(32 * quad + r);
                 if (gi < prm.N && gj <= gi) {
-                  const int2 v = sb[r * 32 + (lane ^ r)];
+                  const int2 v = unbias<EB>(sb[r * 32 + (lane ^ r)], rre, rim, cre, cim);
                   int2* dst = accj + ro[r];
                   if (prm.accumulate) {
                     const int2 o = *dst;
@@ -909,7 +911,8 @@ xcorr_tc8_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant
 #pragma unroll 4
             for (int k = 0; k < 32; ++k) {
               if (tfull || t.tj * kTile + lane_to_input(cc + k) < prm.N) {
-                const int2 v = sb[lane * 32 + (k ^ lane)];
+                const int2 v = unbias<EB>(sb[lane * 32 + (k ^ lane)], row_re, row_im, s.colcorr[cc + k],
+                                          s.colcorr[kTile + cc + k]);
                 int2* dst = acci + s.coloff[cc + k];
                 if (prm.accumulate) {
                   const int2 o = *dst;
