@@ -259,6 +259,16 @@ __device__ __forceinline__ void commit2(uint64_t* bar) {
   asm volatile("tcgen05.commit.cta_group::2.mbarrier::arrive::one.shared::cluster.multicast::cluster.b64 [%0], %1;"
                ::"r"(smem_u32(bar)), "h"(static_cast<uint16_t>(3)) : "memory");
 }
+// L2 prefetch of one tile of a 3-D tensor (no shared-memory destination).
+__device__ __forceinline__ void tma_prefetch_3d(const void* desc, int x, int y, int z) {
+  asm volatile("cp.async.bulk.prefetch.tensor.3d.L2.global.tile [%0, {%1, %2, %3}];"
+               ::"l"(reinterpret_cast<uint64_t>(desc)), "r"(x), "r"(y), "r"(z)
+               : "memory");
+}
+// The raw-tile producers prefetch the tiles kPrefetch stages ahead into L2,
+// so a copy waits for L2 rather than DRAM (e4m3 lwa: 1.035 -> 0.961 ms; 4 and
+// 8 stages ahead, or prefetching into the next unit, measured no better).
+constexpr int kPrefetch = 2;
 // K-major operand, 128-byte swizzle: 8-row groups 1024 B apart.
 __device__ __forceinline__ uint64_t sdesc_k_sw128(uint32_t saddr) {
   uint64_t d = 0;
@@ -504,13 +514,16 @@ xcorr_tc8_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant
             break;
           }
           uint8_t* dst = s.raw + st * G::kRawStage + tile * G::kRawTile;
+          const int kp = ks + kPrefetch * G::kSteps;   // the stage to prefetch into L2
           if (tile == 0) {
             mbar_arrive_expect_tx(&s.raw_full[st], G::kRawTile);
             tma_load_3d(dst, &tmap, &s.raw_full[st], t.ti * kTile, t.c, ks * kStep);
+            if (kp < nks) tma_prefetch_3d(&tmap, t.ti * kTile, t.c, kp * kStep);
           } else if (!own_diag) {
             mbar_arrive_expect_tx(&s.raw_full[st], G::kRawHalf);
             tma_load_3d(dst, &tmap_j, &s.raw_full[st], t.tj * kTile + kHalf * static_cast<int>(rank), t.c,
                         ks * kStep);
+            if (kp < nks) tma_prefetch_3d(&tmap_j, t.tj * kTile + kHalf * static_cast<int>(rank), t.c, kp * kStep);
           } else {
             mbar_arrive(&s.raw_full[st]);    // the I tile serves as J
           }
