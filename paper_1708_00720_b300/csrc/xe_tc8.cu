@@ -18,8 +18,8 @@
 //    memory.  Both CTAs share one J tile, so each unpacks and stores only
 //    half of it and its tensor core reads only half of B from local shared
 //    memory.  Each CTA's 128 x 128 accumulator lives in its own TMEM.
-// Per 32-sample step the pipe of one SM moves ~16 KB of operand B instead of
-// ~32 KB, and the B unpack per SM halves.
+// Per 32-sample e4m3 step the tensor core of one SM reads ~8 KB of operand B
+// from its shared memory instead of ~16 KB, and the B unpack per SM halves.
 //
 // Work: a pair unit is (channel c, J tile, I tile of CTA 0, I tile of
 // CTA 1).  The lower-triangle tile pairs (I >= J) of a channel are grouped
@@ -52,16 +52,18 @@
 //  * MMA (one thread of CTA 0): D_re += A_re B_re^T + A_im B_im^T,
 //                               D_im += A_im B_re^T - A_re B_im^T
 //    (negate-B bit); commits are multicast to both CTAs.
-//  * Epilogue (each CTA): D (single buffer, 256 TMEM columns) is read per
-//    32-column chunk, the bias is removed exactly from per-input sums of u
-//    (the column sums of the other half of J are read from the partner's
-//    shared memory) and rows are written coalesced to the accumulator:
+//  * Epilogue (each CTA): D (single buffer, 256 TMEM columns) is copied out
+//    per 32-column chunk (three chunks to shared staging, one to registers)
+//    and released to the MMA; then the bias is removed exactly from per-input
+//    sums of u (the column sums of the other half of J are read from the
+//    partner's shared memory) and rows are written coalesced to the
+//    accumulator:
 //      Re V = D_re - 8 (P_i + Q_i + P_j + Q_j) + 128 T'
 //      Im V = D_im + 8 (P_i - Q_i) - 8 (P_j - Q_j).
 // Exactness: all partial sums of D stay below 450 T' <= 2^24 for T' <= 37282;
-// the host splits longer gulps into launches of at most 32768 samples.  The
-// number of 32-sample steps per launch is a multiple of 4 (TMA zero-fills the
-// padding, which enters D, the sums and T' consistently).
+// the host splits longer gulps into launches of at most 32768 samples.  A
+// launch covers whole stages (TMA zero-fills the padding, which enters D, the
+// sums and T' consistently).
 #include <cuda.h>
 #include <cuda_runtime.h>
 
