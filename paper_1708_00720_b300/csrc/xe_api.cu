@@ -50,6 +50,7 @@ struct xe_plan {
   long long n_pairs = 0;        // C * nbl complex values
   int32_t* d_acc = nullptr;     // [C][nbl][2]
   int* d_err = nullptr;         // device error word
+  int2* d_split = nullptr;      // scratch of the time-sliced leftover units (tensor-core operands)
   int num_sms = 0;
   long long samples = 0;
   long long launches = 0;
@@ -163,9 +164,12 @@ xe_status enqueue_correlate(xe_plan* p, const uint8_t* d_gulp, int ntime, int ac
     prm.acc = p->d_acc;
     prm.err = p->d_err;
     prm.timeout_ns = kWaitTimeoutNs;
-    cudaError_t e = xe::launch_xcorr_pair(eb, &map, &map_j, prm, p->num_sms, stream);
+    prm.split_ws = p->d_split;
+    prm.split_parts = 0;  // set by the launcher
+    int kernels = 0;
+    cudaError_t e = xe::launch_xcorr_pair(eb, &map, &map_j, prm, p->num_sms, stream, &kernels);
+    p->launches += kernels;
     if (e != cudaSuccess) return cuda_fail(p, e, "tcgen05 launch");
-    ++p->launches;
   }
   return XE_OK;
 }
@@ -251,11 +255,20 @@ xe_status xe_plan_create(xe_plan_t* out, int n_input, int n_chan, int max_ntime,
     delete p;
     return XE_ERR_NOMEM;
   }
+  if (op != XE_OPERAND_INT32_CUDACORE &&
+      cudaMalloc(&p->d_split, xe::split_workspace_bytes(p->num_sms)) != cudaSuccess) {
+    cudaGetLastError();
+    cudaFree(p->d_acc);
+    cudaFree(p->d_err);
+    delete p;
+    return XE_ERR_NOMEM;
+  }
   cudaError_t e1 = cudaMemset(p->d_acc, 0, static_cast<size_t>(p->n_pairs) * 8);
   cudaError_t e2 = cudaMemset(p->d_err, 0, sizeof(int));
   if (e1 != cudaSuccess || e2 != cudaSuccess) {
     cudaFree(p->d_acc);
     cudaFree(p->d_err);
+    if (p->d_split) cudaFree(p->d_split);
     delete p;
     return XE_ERR_CUDA;
   }
@@ -271,6 +284,7 @@ xe_status xe_plan_destroy(xe_plan_t p) {
   cudaDeviceSynchronize();
   cudaFree(p->d_acc);
   cudaFree(p->d_err);
+  if (p->d_split) cudaFree(p->d_split);
   if (p->d_stage) cudaFree(p->d_stage);
   if (p->d_vis_f) cudaFree(p->d_vis_f);
   if (p->s_copy) cudaStreamDestroy(p->s_copy);

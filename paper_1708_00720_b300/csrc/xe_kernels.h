@@ -19,18 +19,28 @@ struct TcParams {
   int32_t* acc;           // [C][N (N + 1) / 2][2] int32 accumulator
   int* err;               // device error word (bit mask of timed-out waits)
   unsigned long long timeout_ns;  // bound on every device-side wait
+  int2* split_ws;         // split_workspace_bytes(max_ctas) of scratch for time-sliced units, or nullptr
+  int split_parts;        // parts per time-sliced leftover unit, 0: none (set by the launcher)
 };
+
+// Scratch of the time-sliced leftover units of one launch on at most
+// max_ctas CTAs: one slot per CTA pair, one 128 x 128 int2 tile per CTA.
+inline size_t split_workspace_bytes(int max_ctas) {
+  return static_cast<size_t>(max_ctas / 2) * 2 * 128 * 128 * sizeof(int2);
+}
 
 // Tensor-core X-engine on pairs of CTAs, operand width eb (1: e4m3, 2:
 // float16).  Both maps view the gulp as uint8 {N, C, T}: tmap_i with box
 // {128, 1, R} and the 128-byte swizzle, tmap_j with box {64, 1, R} and the
 // 64-byte swizzle, R = 128 time rows for e4m3 and 64 for float16.
 // prm.nks must be a multiple of 4 (e4m3) or 2 (float16) 32-sample steps;
-// prm.units is set here (channels x pair units); the grid is at most max_ctas
-// CTAs (an even number).
+// prm.units and prm.split_parts are set here; the grid is at most max_ctas
+// CTAs (an even number).  With prm.split_ws, units left over after the last
+// full round are cut along time over all clusters and summed by a second,
+// small kernel; *kernels receives the number of kernels launched (1 or 2).
 int tc8_smem_bytes(int eb);
 cudaError_t launch_xcorr_pair(int eb, const CUtensorMap* tmap_i, const CUtensorMap* tmap_j, const TcParams& prm,
-                              int max_ctas, cudaStream_t stream);
+                              int max_ctas, cudaStream_t stream, int* kernels);
 
 // Plain CUDA-core correlator (int8 dot products into int32), the baseline.
 cudaError_t launch_xcorr_cudacore(const uint8_t* gulp, int T, int C, int N, int32_t* acc,

@@ -154,7 +154,10 @@ extern "C" XE_API xe_status xe_correlate_noalloc(const uint8_t* d_gulp, int ntim
     prm.acc = d_acc;
     prm.err = d_err;
     prm.timeout_ns = kWaitTimeoutNs;
-    if (xe::launch_xcorr_pair(1, &map, &map_j, prm, sms, s) != cudaSuccess) return XE_ERR_CUDA;
+    prm.split_ws = nullptr;  // no scratch for time slices here: leftover units run whole
+    prm.split_parts = 0;
+    int kernels = 0;
+    if (xe::launch_xcorr_pair(1, &map, &map_j, prm, sms, s, &kernels) != cudaSuccess) return XE_ERR_CUDA;
   }
   cudaError_t e = (out_type == XE_OUT_CI32)
                       ? cudaMemcpyAsync(d_vis, d_acc, out_bytes, cudaMemcpyDeviceToDevice, s)

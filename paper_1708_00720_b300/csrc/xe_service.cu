@@ -480,8 +480,10 @@ XE_API xe_status xe_service_add_stream(xe_service_t svc, const xe_stream_config*
   s->gulp_bytes = static_cast<size_t>(c.gulp_ntime) * c.n_chan * c.n_input;
   const long long nbl = static_cast<long long>(c.n_input) * (c.n_input + 1) / 2;
   s->vis_bytes = static_cast<size_t>(c.n_chan) * nbl * 8;
-  // device: ring + plan accumulator + visibility buffer (+1 MiB of plan workspace)
-  s->dev_bytes = static_cast<long long>(c.ring_gulps) * s->gulp_bytes + 2LL * s->vis_bytes + (1LL << 20);
+  // device: ring + plan accumulator + visibility buffer + the plan's scratch
+  // for time-sliced units (as on a 148-SM B300) + 1 MiB of other plan memory
+  s->dev_bytes = static_cast<long long>(c.ring_gulps) * s->gulp_bytes + 2LL * s->vis_bytes +
+                 static_cast<long long>(xe::split_workspace_bytes(148)) + (1LL << 20);
   s->host_bytes = static_cast<long long>(c.ring_gulps) * s->gulp_bytes + kOutSlots * static_cast<long long>(s->vis_bytes);
   std::lock_guard<std::mutex> lk(S.mu);
   if (S.used + s->dev_bytes > S.cap) {

@@ -103,6 +103,7 @@ constexpr int kSlotInts = 2 * kTile + 2 * kHalf;  // P_I, Q_I (128 each), P_J, Q
 constexpr int kSumsBytes = 2 * kSlotInts * 4 + 2 * kTile * 4 + 2 * kTile * 4;
 // 2 slots of sums, column corrections (re, im), row and column triangle offsets
 constexpr int kNumBars = 2 * kRawStages + 2 * kOpStages + 2 + 2 + 2 + 1;
+constexpr int kCtlBytes = 64;   // after the barriers: TMEM address, abort flag, schedule
 
 // Operand width EB (1: e4m3, 2: f16) sets the samples per stage and the raw tiles.
 template <int EB>
@@ -113,7 +114,7 @@ struct Geo {
   static constexpr int kRawStage = kRawTile + kRawHalf; // I box (128-byte rows), half J box (64-byte rows)
   static constexpr int kRawBytes = kRawStages * kRawStage;
   static constexpr int kBarOffset = kOpBytes + kRawBytes + kStageBytes + kSumsBytes;
-  static constexpr int kSmemBytes = kBarOffset + kNumBars * 8 + 16 + 1024;
+  static constexpr int kSmemBytes = kBarOffset + kNumBars * 8 + kCtlBytes + 1024;
   static_assert(kSmemBytes <= 227 * 1024, "shared memory budget");
   static_assert(kOpBytes % 1024 == 0 && kRawStage % 1024 == 0, "swizzled tiles need 1024-byte alignment");
 };
@@ -157,6 +158,7 @@ struct Smem {
   uint64_t *acc_full, *acc_empty, *sums_full, *sums_empty, *final_bar;
   uint32_t* tmem_slot;
   int* abort_flag;
+  int* sched;      // schedule header and tail items (item_at)
 };
 
 template <int EB>
@@ -182,6 +184,7 @@ __device__ __forceinline__ Smem carve(uint8_t* base) {
   p.final_bar = b; b += 1;
   p.tmem_slot = reinterpret_cast<uint32_t*>(b);
   p.abort_flag = reinterpret_cast<int*>(b) + 1;
+  p.sched = reinterpret_cast<int*>(b) + 2;
   return p;
 }
 
@@ -326,6 +329,83 @@ __device__ __forceinline__ Unit decode_unit(int u, int per_chan, int nt, int ran
     t.transposed = true;
   }
   return t;
+}
+
+// ------------------------------------------------------------ schedule
+// Cluster cl runs the pair units cl, cl + ncl, ... of the R = units / ncl
+// full rounds.  The L = units % ncl units left over would keep L clusters
+// busy for a whole unit more while the rest idle, so each is cut along time
+// into q = ncl / L nearly equal parts (stages [S i / q, S (i + 1) / q) of its
+// S, i < q), and cluster cl < q L takes part cl % q of leftover unit cl / q:
+// one part per cluster, since a second one would wait for the first one's
+// accumulator to be drained.  A part is reduced like a unit of its own (its
+// own sums of u and sample count T') and its exact integer block is stored,
+// in the epilogue's usual write pattern, into the cluster's workspace slot
+// (one 128 x 128 int2 tile per CTA: row a = accumulator row of the output
+// tile in lane order, column b = input offset in the tile).
+// split_combine_kernel then adds the q parts of each leftover unit and
+// writes the sum as a unit's epilogue would.  All sums are integer, so their
+// order does not matter.
+constexpr int kMinPartSamples = 1024;        // shortest part worth its own epilogue
+constexpr int kSplitTile = kTile * kTile;    // int2 per CTA and workspace slot
+
+struct Item {
+  int u;        // pair unit
+  int k0, k1;   // its 32-sample steps [k0, k1)
+  int lo;       // leftover unit index of a part, else -1
+};
+
+// Schedule of this cluster in shared memory: {items, R, cl, ncl, nks} and
+// then the item after the R full rounds, if any, as {u, k0, k1, lo}.
+constexpr int kSchedInts = 5 + 4;
+static_assert((2 + kSchedInts) * 4 <= kCtlBytes, "control words after the barriers");
+__device__ inline void fill_sched(int* sc, int units, int cl, int ncl, int nks, int steps, int q) {
+  const int R = units / ncl, L = units - R * ncl, S = nks / steps;
+  int n = 0;
+  int* t = sc + 5;
+  if (q == 0 && cl < L) {
+    t[0] = R * ncl + cl; t[1] = 0; t[2] = nks; t[3] = -1;
+    n = 1;
+  } else if (q > 0 && cl < q * L) {
+    const int l = cl / q, i = cl - l * q;
+    t[0] = R * ncl + l; t[1] = S * i / q * steps; t[2] = S * (i + 1) / q * steps; t[3] = l;
+    n = 1;
+  }
+  sc[0] = R + n;
+  sc[1] = R;
+  sc[2] = cl;
+  sc[3] = ncl;
+  sc[4] = nks;
+}
+
+// Item i of this cluster (the schedule is read from shared memory each time:
+// registers are scarce in every warp role).
+__device__ __forceinline__ Item item_at(const int* sc, int i) {
+  Item w;
+  const int R = sc[1];
+  if (i < R) {
+    w.u = sc[2] + i * sc[3];
+    w.k0 = 0;
+    w.k1 = sc[4];
+    w.lo = -1;
+  } else {
+    w.u = sc[5];
+    w.k0 = sc[6];
+    w.k1 = sc[7];
+    w.lo = sc[8];
+  }
+  return w;
+}
+
+// Parts q per leftover unit (0: run the leftover units whole).
+__host__ inline int split_parts(long long units, long long clusters, int nks, int steps) {
+  const long long L = units % clusters;
+  if (L == 0) return 0;
+  long long min_part = kMinPartSamples / (steps * kStep);
+  if (min_part < 1) min_part = 1;
+  long long q = clusters / L;
+  if (q > (nks / steps) / min_part) q = (nks / steps) / min_part;
+  return q >= 2 ? static_cast<int>(q) : 0;
 }
 
 // ------------------------------------------------------------------ unpack
@@ -483,6 +563,7 @@ xcorr_tc8_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant
     }
     mbar_init(s.final_bar, 1);
     *s.abort_flag = 0;
+    fill_sched(s.sched, prm.units, cl, ncl, nks, G::kSteps, prm.split_parts);
     mbar_fence_init();
     tma_prefetch_desc(&tmap);
     tma_prefetch_desc(&tmap_j);
@@ -505,10 +586,11 @@ xcorr_tc8_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant
       const int tile = warp >> 1;               // 0: I tiles, 1: J tiles
       int rit = 0;                              // raw stage counter (4 steps each)
       bool ok = true;
-      for (int u = cl; u < prm.units && ok; u += ncl) {
-        const Unit t = decode_unit(u, per_chan, nt, rank);
+      for (int it = 0; it < s.sched[0] && ok; ++it) {
+        const Item w = item_at(s.sched, it);
+        const Unit t = decode_unit(w.u, per_chan, nt, rank);
         const bool own_diag = (t.ti == t.tj);
-        for (int ks = 0; ks < nks; ks += G::kSteps, ++rit) {
+        for (int ks = w.k0; ks < w.k1; ks += G::kSteps, ++rit) {
           const int st = rit % kRawStages;
           if (!wait_or_abort(&s.raw_empty[st], ((rit / kRawStages) & 1) ^ 1, lim, abort_flag)) {
             fail(s, prm.err, kErrWaitRawEmpty);
@@ -520,12 +602,12 @@ xcorr_tc8_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant
           if (tile == 0) {
             mbar_arrive_expect_tx(&s.raw_full[st], G::kRawTile);
             tma_load_3d(dst, &tmap, &s.raw_full[st], t.ti * kTile, t.c, ks * kStep);
-            if (kp < nks) tma_prefetch_3d(&tmap, t.ti * kTile, t.c, kp * kStep);
+            if (kp < w.k1) tma_prefetch_3d(&tmap, t.ti * kTile, t.c, kp * kStep);
           } else if (!own_diag) {
             mbar_arrive_expect_tx(&s.raw_full[st], G::kRawHalf);
             tma_load_3d(dst, &tmap_j, &s.raw_full[st], t.tj * kTile + kHalf * static_cast<int>(rank), t.c,
                         ks * kStep);
-            if (kp < nks) tma_prefetch_3d(&tmap_j, t.tj * kTile + kHalf * static_cast<int>(rank), t.c, kp * kStep);
+            if (kp < w.k1) tma_prefetch_3d(&tmap_j, t.tj * kTile + kHalf * static_cast<int>(rank), t.c, kp * kStep);
           } else {
             mbar_arrive(&s.raw_full[st]);    // the I tile serves as J
           }
@@ -543,8 +625,9 @@ xcorr_tc8_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant
     if (lane == 0) {
       int sit = 0;
       bool ok = true;
-      for (int u = cl; u < prm.units && ok; u += ncl) {
-        for (int ks = 0; ks < nks; ks += G::kSteps, ++sit) {
+      for (int it = 0; it < s.sched[0] && ok; ++it) {
+        const Item w = item_at(s.sched, it);
+        for (int ks = w.k0; ks < w.k1; ks += G::kSteps, ++sit) {
           const int st = sit % kOpStages;
           if (!wait_or_abort(&s.op_full[st], (sit / kOpStages) & 1, lim, abort_flag)) {
             fail(s, prm.err, kErrWaitOpFull);
@@ -564,13 +647,14 @@ xcorr_tc8_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant
       constexpr uint32_t id_pos = (1u << 4) | ((128u >> 3) << 17) | ((256u >> 4) << 24);
       constexpr uint32_t id_neg = id_pos | (1u << 14);
       const uint32_t d_re = tmem, d_im = tmem + 128;
-      for (int u = cl; u < prm.units && ok; u += ncl, ++ui) {
+      for (int it = 0; it < s.sched[0] && ok; ++it, ++ui) {
+        const Item w = item_at(s.sched, it);
         if (!wait_or_abort(s.acc_empty, (ui & 1) ^ 1, lim, abort_flag)) {
           fail(s, prm.err, kErrWaitAccEmpty);
           break;
         }
         tc_fence_after();
-        for (int ks = 0; ks < nks; ks += G::kSteps, ++sit) {
+        for (int ks = w.k0; ks < w.k1; ks += G::kSteps, ++sit) {
           const int st = sit % kOpStages;
           if (!wait_or_abort(&s.op_full[st], (sit / kOpStages) & 1, lim, abort_flag)) {
             fail(s, prm.err, kErrWaitOpFull);
@@ -587,7 +671,7 @@ xcorr_tc8_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant
               const uint32_t a_re = a0 + 16 * sub, a_im = a_re + 8;
               const uint64_t b_re = sdesc_k_sw128(op + 32 * sub);
               const uint64_t b_im = sdesc_k_sw128(op + kPlane + 32 * sub);
-              const uint32_t acc0 = (ks + sub) > 0 ? 1u : 0u;
+              const uint32_t acc0 = (ks - w.k0 + sub) > 0 ? 1u : 0u;
               mma2_f8_tmem_a(d_re, a_re, b_re, id_pos, acc0);
               mma2_f8_tmem_a(d_re, a_im, b_im, id_pos, 1u);
               mma2_f8_tmem_a(d_im, a_im, b_re, id_pos, acc0);
@@ -603,7 +687,7 @@ xcorr_tc8_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant
                 const uint32_t a_re = a0 + 32 * sub + 8 * kk, a_im = a_re + 16;
                 const uint64_t b_re = sdesc_k_sw128(op + 64 * sub + 32 * kk);
                 const uint64_t b_im = sdesc_k_sw128(op + kPlane + 64 * sub + 32 * kk);
-                const uint32_t acc0 = (ks + sub + kk) > 0 ? 1u : 0u;
+                const uint32_t acc0 = (ks - w.k0 + sub + kk) > 0 ? 1u : 0u;
                 mma2_f16_tmem_a(d_re, a_re, b_re, id_pos, acc0);
                 mma2_f16_tmem_a(d_re, a_im, b_im, id_pos, 1u);
                 mma2_f16_tmem_a(d_im, a_im, b_re, id_pos, acc0);
@@ -626,11 +710,12 @@ xcorr_tc8_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant
     const uint32_t lane_off = static_cast<uint32_t>(32 * quad + 16 * h) << 16;
     int sit = 0, ui = 0;
     bool ok = true;
-    for (int u = cl; u < prm.units && ok; u += ncl, ++ui) {
+    for (int it = 0; it < s.sched[0] && ok; ++it, ++ui) {
+      const Item w = item_at(s.sched, it);
       PairSums ps;
       ps.zero();
       int since_fold = 0;
-      for (int ks = 0; ks < nks; ks += G::kSteps, ++sit) {
+      for (int ks = w.k0; ks < w.k1; ks += G::kSteps, ++sit) {
         const int rst = sit % kRawStages, ost = sit % kOpStages;
         if (!wait_or_abort(&s.raw_full[rst], (sit / kRawStages) & 1, lim, abort_flag)) {
           fail(s, prm.err, kErrWaitRawFull);
@@ -672,7 +757,7 @@ xcorr_tc8_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant
           mbar_arrive(&s.op_full[ost]);
           mbar_arrive(&s.raw_empty[rst]);
         }
-        if (++since_fold == 2 || ks + G::kSteps >= nks) {
+        if (++since_fold == 2 || ks + G::kSteps >= w.k1) {
           ps.fold();
           since_fold = 0;
         }
@@ -705,13 +790,14 @@ xcorr_tc8_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant
     const int kq = lane & 3;                   // 8-byte K segment of each step
     int sit = 0, ui = 0;
     bool ok = true;
-    for (int u = cl; u < prm.units && ok; u += ncl, ++ui) {
-      const Unit t = decode_unit(u, per_chan, nt, rank);
+    for (int it = 0; it < s.sched[0] && ok; ++it, ++ui) {
+      const Item w = item_at(s.sched, it);
+      const Unit t = decode_unit(w.u, per_chan, nt, rank);
       const bool own_diag = (t.ti == t.tj);
       PairSums ps;
       ps.zero();
       int since_fold = 0;
-      for (int ks = 0; ks < nks; ks += G::kSteps, ++sit) {
+      for (int ks = w.k0; ks < w.k1; ks += G::kSteps, ++sit) {
         const int rst = sit % kRawStages, ost = sit % kOpStages;
         if (!wait_or_abort(&s.raw_full[rst], (sit / kRawStages) & 1, lim, abort_flag)) {
           fail(s, prm.err, kErrWaitRawFull);
@@ -766,7 +852,7 @@ xcorr_tc8_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant
           mbar_arrive(&s.op_full[ost]);
           mbar_arrive(&s.raw_empty[rst]);
         }
-        if (++since_fold == 2 || ks + G::kSteps >= nks) {
+        if (++since_fold == 2 || ks + G::kSteps >= w.k1) {
           ps.fold();
           since_fold = 0;
         }
@@ -801,13 +887,14 @@ xcorr_tc8_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant
     const int quad = warp & 3;
     const int L = 32 * quad + lane;                 // TMEM lane = accumulator row; also a column index
     const int il = lane_to_input(L);                // input offset of row / column L in its tile
-    const int T_pad = nks * kStep;
     const long long nbl = static_cast<long long>(prm.N) * (prm.N + 1) / 2;
     int2* stg = s.stage + quad * kStageBufs * 32 * 32;
     bool ok = true;
     int ui = 0;
-    for (int u = cl; u < prm.units; u += ncl, ++ui) {
-      const Unit t = decode_unit(u, per_chan, nt, rank);
+    for (int it = 0; it < s.sched[0]; ++it, ++ui) {
+      const Item w = item_at(s.sched, it);
+      const Unit t = decode_unit(w.u, per_chan, nt, rank);
+      const int T_pad = (w.k1 - w.k0) * kStep;
       const int slot = ui & 1;
       if (ok && !wait_or_abort(&s.sums_full[slot], (ui >> 1) & 1, lim, abort_flag)) {
         fail(s, prm.err, kErrWaitSumsFull);
@@ -828,11 +915,15 @@ xcorr_tc8_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant
         s.colcorr[L] = static_cast<float>(-8 * (pjv + qjv));
         s.colcorr[kTile + L] = static_cast<float>(-8 * (pjv - qjv));
       }
-      {
+      if (w.lo < 0) {
         // packed-triangle offsets of row L's and column L's inputs (N <= 8192 fits int)
         const int gi = t.ti * kTile + il, gj = t.tj * kTile + il;
         s.rowoff[L] = gi < prm.N ? gi * (gi + 1) / 2 : 0;
         s.coloff[L] = gj < prm.N ? gj * (gj + 1) / 2 : 0;
+      } else {
+        // a part: rows of the compact workspace tile
+        s.rowoff[L] = L * kTile;
+        s.coloff[L] = L * kTile;
       }
       asm volatile("bar.sync 1, 128;" ::: "memory");
       if (lane == 0) {   // this slot's own sums and the partner's half of J have been read
@@ -848,8 +939,13 @@ xcorr_tc8_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant
       if (ok && t.write) {
         tc_fence_after();
         const uint32_t t_row = tmem + (static_cast<uint32_t>(32 * quad) << 16);
-        const long long chan_base = static_cast<long long>(t.c) * nbl;
-        int2* const acc = reinterpret_cast<int2*>(prm.acc) + chan_base;
+        // a part goes to its workspace slot (stored, never added): the tile's
+        // first column input then lands on column 0
+        const int accumulate = w.lo < 0 ? prm.accumulate : 0;
+        int2* const acc =
+            w.lo < 0 ? reinterpret_cast<int2*>(prm.acc) + static_cast<long long>(t.c) * nbl
+                     : prm.split_ws + (static_cast<long long>(2 * cl + rank) * kSplitTile -
+                                       (t.transposed ? t.ti : t.tj) * kTile);
         // a tile strictly below the diagonal and inside N needs no checks
         const bool full = !t.transposed && t.ti > t.tj && t.ti * kTile + kTile <= prm.N;
         const bool tfull = t.transposed && t.tj * kTile + kTile <= prm.N;
@@ -886,7 +982,7 @@ xcorr_tc8_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant
             const int gj = t.tj * kTile + lane_to_input(cc + lane);
             const float cre = s.colcorr[cc + lane], cim = s.colcorr[kTile + cc + lane];
             int2* accj = acc + gj;
-            if (full && !prm.accumulate) {
+            if (full && !accumulate) {
 #pragma unroll 4
               for (int r = 0; r < 32; ++r) {
                 const float rre = __shfl_sync(0xFFFFFFFFu, row_re, r), rim = __shfl_sync(0xFFFFFFFFu, row_im, r);
@@ -909,7 +1005,7 @@ xcorr_tc8_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant
                 if (gi < prm.N && gj <= gi) {
                   const int2 v = unbias<EB>(sb[r * 32 + (lane ^ r)], rre, rim, cre, cim);
                   int2* dst = accj + ro[r];
-                  if (prm.accumulate) {
+                  if (accumulate) {
                     const int2 o = *dst;
                     *dst = make_int2(o.x + v.x, o.y + v.y);
                   } else {
@@ -929,7 +1025,7 @@ xcorr_tc8_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant
                 const int2 v = unbias<EB>(sb[lane * 32 + (k ^ lane)], row_re, row_im, s.colcorr[cc + k],
                                           s.colcorr[kTile + cc + k]);
                 int2* dst = acci + s.coloff[cc + k];
-                if (prm.accumulate) {
+                if (accumulate) {
                   const int2 o = *dst;
                   *dst = make_int2(o.x + v.x, o.y - v.y);
                 } else {
@@ -967,6 +1063,50 @@ xcorr_tc8_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant
   }
 }
 
+// Sum of the time-sliced parts of the leftover units.  Block (x, y): x =
+// leftover unit l (x / 2) and CTA rank of its pair (x % 2), y = group of 8
+// accumulator rows of that CTA's tile; each warp takes one row.  The q parts
+// of unit l are in the workspace slots of clusters l q .. l q + q - 1.
+struct CombineParams {
+  int N, nt, per_chan, units, ncl, q, accumulate;
+  int32_t* acc;
+  const int2* ws;
+};
+
+__global__ void __launch_bounds__(256) split_combine_kernel(const CombineParams p) {
+  const int l = blockIdx.x >> 1, rank = blockIdx.x & 1;
+  const Unit t = decode_unit(p.units - p.units % p.ncl + l, p.per_chan, p.nt, rank);
+  if (!t.write) return;
+  // the output tile: rows Rt * 128 + lane_to_input(a), columns Ct * 128 + b, j <= i < N
+  const int Rt = t.transposed ? t.tj : t.ti, Ct = t.transposed ? t.ti : t.tj;
+  const int a = 8 * blockIdx.y + (threadIdx.x >> 5), lane = threadIdx.x & 31;
+  const int gi = Rt * kTile + lane_to_input(a);
+  if (gi >= p.N) return;
+  int2* orow = reinterpret_cast<int2*>(p.acc) + static_cast<long long>(t.c) * p.N * (p.N + 1) / 2 + gi * (gi + 1) / 2;
+  int sx[4] = {0, 0, 0, 0}, sy[4] = {0, 0, 0, 0};
+  for (int c = l * p.q; c < (l + 1) * p.q; ++c) {
+    const int2* src = p.ws + static_cast<long long>(2 * c + rank) * kSplitTile + a * kTile;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const int2 v = src[lane + 32 * k];
+      sx[k] += v.x;
+      sy[k] += v.y;
+    }
+  }
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const int gj = Ct * kTile + lane + 32 * k;
+    if (gj > gi) break;
+    int2* d = orow + gj;
+    if (p.accumulate) {
+      const int2 o = *d;
+      *d = make_int2(o.x + sx[k], o.y + sy[k]);
+    } else {
+      *d = make_int2(sx[k], sy[k]);
+    }
+  }
+}
+
 }  // namespace tc8
 
 int tc8_smem_bytes(int eb) { return eb == 1 ? tc8::Geo<1>::kSmemBytes : tc8::Geo<2>::kSmemBytes; }
@@ -974,7 +1114,8 @@ int tc8_smem_bytes(int eb) { return eb == 1 ? tc8::Geo<1>::kSmemBytes : tc8::Geo
 namespace {
 template <int EB>
 cudaError_t launch_pair(const CUtensorMap* tmap_i, const CUtensorMap* tmap_j, TcParams prm, int max_ctas,
-                        cudaStream_t stream) {
+                        cudaStream_t stream, int* kernels) {
+  *kernels = 0;
   constexpr int smem = tc8::Geo<EB>::kSmemBytes;
   cudaError_t e = cudaFuncSetAttribute(tc8::xcorr_tc8_kernel<EB>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
@@ -999,15 +1140,36 @@ cudaError_t launch_pair(const CUtensorMap* tmap_i, const CUtensorMap* tmap_j, Tc
   if (resident_clusters > 0 && resident_clusters < clusters) clusters = resident_clusters;
   if (units < clusters) clusters = units;
   if (clusters < 1) clusters = 1;
+  prm.split_parts = prm.split_ws ? tc8::split_parts(units, clusters, prm.nks, tc8::Geo<EB>::kSteps) : 0;
   tc8::xcorr_tc8_kernel<EB><<<static_cast<int>(2 * clusters), tc8::kThreads, smem, stream>>>(*tmap_i, *tmap_j, prm);
-  return cudaGetLastError();
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  *kernels = 1;
+  if (prm.split_parts > 0) {
+    tc8::CombineParams q;
+    q.N = prm.N;
+    q.nt = prm.nt;
+    q.per_chan = tc8::pairs_per_channel(prm.nt);
+    q.units = prm.units;
+    q.ncl = static_cast<int>(clusters);
+    q.q = prm.split_parts;
+    q.accumulate = prm.accumulate;
+    q.acc = prm.acc;
+    q.ws = prm.split_ws;
+    const int L = static_cast<int>(units % clusters);
+    tc8::split_combine_kernel<<<dim3(2 * L, tc8::kTile / 8), 256, 0, stream>>>(q);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    *kernels = 2;
+  }
+  return cudaSuccess;
 }
 }  // namespace
 
 cudaError_t launch_xcorr_pair(int eb, const CUtensorMap* tmap_i, const CUtensorMap* tmap_j, const TcParams& prm,
-                              int max_ctas, cudaStream_t stream) {
-  return eb == 1 ? launch_pair<1>(tmap_i, tmap_j, prm, max_ctas, stream)
-                 : launch_pair<2>(tmap_i, tmap_j, prm, max_ctas, stream);
+                              int max_ctas, cudaStream_t stream, int* kernels) {
+  return eb == 1 ? launch_pair<1>(tmap_i, tmap_j, prm, max_ctas, stream, kernels)
+                 : launch_pair<2>(tmap_i, tmap_j, prm, max_ctas, stream, kernels);
 }
 
 }  // namespace xe

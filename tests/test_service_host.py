@@ -11,9 +11,14 @@ from paper_1708_00720_b300 import xengine as xe
 MiB = 1 << 20
 
 
+# scratch of the time-sliced leftover units of a plan on a 148-SM B300:
+# one slot per CTA pair, one 128 x 128 int2 tile per CTA
+SPLIT_WS = 74 * 2 * 128 * 128 * 8
+
+
 def dev_bytes(N, C, T, R):
     nbl = N * (N + 1) // 2
-    return R * T * C * N + 2 * C * nbl * 8 + MiB
+    return R * T * C * N + 2 * C * nbl * 8 + SPLIT_WS + MiB
 
 
 def mk(manual=True, cap=1 << 34):
@@ -28,8 +33,8 @@ def put(s, sid, seq):
 
 
 def test_admission_against_the_cap():
-    need = dev_bytes(64, 32, 128, 4)
-    s = mk(cap=2 * need + need // 2)
+    need, small = dev_bytes(64, 32, 128, 4), dev_bytes(16, 1, 16, 1)
+    s = mk(cap=2 * need + small + (need - small) // 2)
     a = s.add_stream(64, 32, 128, ring_gulps=4)
     b = s.add_stream(64, 32, 128, ring_gulps=4)
     assert s.stats(a)["device_bytes"] == need and s.stats(b)["device_bytes"] == need

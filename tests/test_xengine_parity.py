@@ -6,6 +6,8 @@ are compared in full; the full-size workloads are compared on sampled
 baselines computed one by one by the oracle, plus properties that hold at
 any size.
 """
+import functools
+
 import numpy as np
 import pytest
 
@@ -102,6 +104,45 @@ def test_all_minus_eight(xe, operand):
 def test_gulp_longer_than_one_launch(xe, operand):
     x = synth.voltages(32, 2, 40000, seed=3)
     np.testing.assert_array_equal(run(xe, x, operand), oracle.correlate(x))
+
+
+# Shapes whose pair units do not fill whole rounds of the 74 CTA pairs of a
+# 148-SM B300: the units left over are cut along time over all pairs, each
+# slice reduced with its own bias corrections and added with integer atomics
+# (into a tile that the first slice to finish zeroes, when overwriting).
+SPLIT_SHAPES = [  # (N, C, T)
+    (16, 75, 4096),    # one unit per channel, one left over
+    (16, 96, 4096),    # 22 left over, as at 512 inputs x 256 channels
+    (144, 38, 2048),   # two units per channel; a leftover one repeats a tile unwritten
+    (272, 25, 2048),   # three per channel; the leftover one holds a transposed tile
+]
+
+
+@functools.lru_cache(maxsize=None)
+def _split_case(shape):
+    N, C, T = shape
+    x = synth.voltages(N, C, T, seed=N + 3 * C + T, random_phase=True)
+    return x, oracle.correlate(x)
+
+
+@pytest.mark.parametrize("operand", ["fp8", "fp16"])
+@pytest.mark.parametrize("shape", SPLIT_SHAPES, ids=lambda s: "x".join(map(str, s)))
+def test_time_sliced_leftover_units(xe, operand, shape):
+    import torch
+    N, C, T = shape
+    x, ref = _split_case(shape)
+    eng = xe.XEngine(N, C, T, operand)
+    g = torch.from_numpy(x).cuda()
+    for _ in range(2):   # the tiles' claim words must be back to zero for the second launch
+        eng.correlate(g)
+        v = eng.integrate().cpu().numpy()
+        eng.check()
+        np.testing.assert_array_equal(v, ref)
+    eng.correlate(g, accumulate=True)
+    v = eng.integrate().cpu().numpy()
+    eng.check()
+    np.testing.assert_array_equal(v, 2 * ref)
+    eng.close()
 
 
 @pytest.mark.parametrize("operand", OPS)
