@@ -56,7 +56,7 @@ KERNEL_SOURCES = {
     "xcorr_tc_fp16": ["paper_1708_00720_b300/csrc/xe_tc8.cu", "paper_1708_00720_b300/csrc/xe_ptx.cuh"],
     "xcorr_cudacore": ["paper_1708_00720_b300/csrc/xe_cudacore.cu"],
     "calib_pass": ["paper_1708_00720_b300/csrc/xe_calib.cu"],
-    "beam_kernel": ["paper_1708_00720_b300/csrc/xe_beam.cu", "paper_1708_00720_b300/csrc/xe_ptx.cuh"],
+    "beam8_kernel": ["paper_1708_00720_b300/csrc/xe_beam8.cu", "paper_1708_00720_b300/csrc/xe_ptx.cuh"],
 }
 
 
@@ -462,7 +462,8 @@ def link_peak_gbs(dev) -> tuple[float, float]:
 
 def beam_bytes(N, C, T, B) -> int:
     """Algorithmic bytes of one beamforming pass: the gulp (1 B per sample),
-    the beams (8 B per complex64 output) and the float16 operand weights."""
+    the beams (8 B per complex64 output) and the weights at their float16
+    operand precision (the kernel's e4m3 term images are twice that)."""
     npad = -(-N // 64) * 64
     return T * C * N + T * C * B * 8 + C * 2 * B * 2 * npad * 2
 
@@ -556,8 +557,8 @@ def run_beam(args, world, rank, local, pg, dev):
                        "parallelism": f"weak, {world} independent gulps"},
             "input_gbs": world * x.nbytes / (ms * 1e-3) / 1e9,
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm"], "unit": "GB/s",
-                         "frac": achieved / peaks["hbm"], "traffic": recorded_traffic("beam_kernel"),
-                         "kernel": "beam_kernel",
+                         "frac": achieved / peaks["hbm"], "traffic": recorded_traffic("beam8_kernel"),
+                         "kernel": "beam8_kernel",
                          "kernel_ms": call_ms, "algorithmic_bytes_per_launch": nbytes,
                          "peak_source": f"{peaks['source']} HBM copy bandwidth"},
             "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": args.steps, "clocks": clk.summary(),

@@ -583,8 +583,14 @@ struct xe_beam {
   int N = 0, C = 0, B = 0, S = 0, max_ntime = 0;
   int num_sms = 0;
   bool weights_set = false;
-  uint16_t* d_wt = nullptr;
-  float* d_bias = nullptr;
+  // time along N (xe_beam8.cu) when B <= 16 and N <= 512, else time along M
+  bool t_on_n = false;
+  int S8 = 0;                   // 128-input stages of the time-along-N kernel
+  uint16_t* d_wt = nullptr;     // time along M: float16 operand tiles
+  float* d_bias = nullptr;      // [C][2B] (time along M) or [C][32] (time along N)
+  uint8_t* d_wa = nullptr;      // time along N: e4m3 operand-A images
+  float* d_sigma = nullptr;     // time along N: per-channel weight scale
+  float* d_osc = nullptr;       // time along N: 2^9 / sigma
   int* d_err = nullptr;
   long long launches = 0;
   std::string last_error;
@@ -593,6 +599,42 @@ struct xe_beam {
 namespace {
 constexpr unsigned long long kBeamTimeoutNs = 2000000000ull;
 bool aligned_to(const void* p, uintptr_t a) { return (reinterpret_cast<uintptr_t>(p) & (a - 1)) == 0; }
+
+// One gulp through the time-along-N kernel (validated arguments).
+xe_status form_t_on_n(xe_beam* b, const uint8_t* d_gulp, int ntime, float* d_out, cudaStream_t stream) {
+  CUtensorMap map;
+  const unsigned long long dims[3] = {static_cast<unsigned long long>(b->N), static_cast<unsigned long long>(b->C),
+                                      static_cast<unsigned long long>(ntime)};
+  const unsigned long long strides[2] = {static_cast<unsigned long long>(b->N),
+                                         static_cast<unsigned long long>(b->N) * b->C};
+  const unsigned box[3] = {128, 1, 128};
+  if (!xe::encode_tensor_u8(&map, d_gulp, 3, dims, strides, box, 128)) {
+    b->last_error = "cuTensorMapEncodeTiled failed";
+    return XE_ERR_CUDA;
+  }
+  xe::Beam8Params prm;
+  prm.N = b->N;
+  prm.C = b->C;
+  prm.B = b->B;
+  prm.S = b->S8;
+  prm.T = ntime;
+  prm.tiles = (ntime + 127) / 128;
+  prm.wa = b->d_wa;
+  prm.osc = b->d_osc;
+  prm.bias = b->d_bias;
+  prm.out = d_out;
+  prm.err = b->d_err;
+  prm.timeout_ns = kBeamTimeoutNs;
+  const long long units = static_cast<long long>(b->C) * prm.tiles;
+  const int grid = static_cast<int>(units < b->num_sms ? units : b->num_sms);
+  const cudaError_t e = xe::launch_beam8(&map, prm, grid, stream);
+  if (e != cudaSuccess) {
+    b->last_error = std::string("beam launch: ") + cudaGetErrorString(e);
+    return XE_ERR_CUDA;
+  }
+  ++b->launches;
+  return XE_OK;
+}
 }  // namespace
 
 extern "C" {
@@ -618,15 +660,28 @@ XE_API xe_status xe_beam_create(xe_beam_t* out, int n_input, int n_chan, int n_b
   b->S = (n_input + 63) / 64;
   b->max_ntime = max_ntime;
   b->num_sms = sms;
-  const size_t wt_bytes = static_cast<size_t>(n_chan) * b->S * xe::bm::w_stage_bytes(n_beam);
-  bool ok = cudaMalloc(&b->d_wt, wt_bytes) == cudaSuccess;
-  ok = ok && cudaMalloc(&b->d_bias, static_cast<size_t>(n_chan) * 2 * n_beam * sizeof(float)) == cudaSuccess;
+  b->t_on_n = n_beam <= 16 && n_input <= 512;
+  b->S8 = (n_input + 127) / 128;
+  bool ok = true;
+  if (b->t_on_n) {
+    ok = cudaMalloc(&b->d_wa, static_cast<size_t>(n_chan) * 128 * 256 * b->S8) == cudaSuccess;
+    ok = ok && cudaMalloc(&b->d_sigma, static_cast<size_t>(n_chan) * sizeof(float)) == cudaSuccess;
+    ok = ok && cudaMalloc(&b->d_osc, static_cast<size_t>(n_chan) * sizeof(float)) == cudaSuccess;
+    ok = ok && cudaMalloc(&b->d_bias, static_cast<size_t>(n_chan) * 32 * sizeof(float)) == cudaSuccess;
+  } else {
+    const size_t wt_bytes = static_cast<size_t>(n_chan) * b->S * xe::bm::w_stage_bytes(n_beam);
+    ok = cudaMalloc(&b->d_wt, wt_bytes) == cudaSuccess;
+    ok = ok && cudaMalloc(&b->d_bias, static_cast<size_t>(n_chan) * 2 * n_beam * sizeof(float)) == cudaSuccess;
+  }
   ok = ok && cudaMalloc(&b->d_err, sizeof(int)) == cudaSuccess;
   ok = ok && cudaMemset(b->d_err, 0, sizeof(int)) == cudaSuccess;
   if (!ok) {
     cudaGetLastError();
     cudaFree(b->d_wt);
     cudaFree(b->d_bias);
+    cudaFree(b->d_wa);
+    cudaFree(b->d_sigma);
+    cudaFree(b->d_osc);
     cudaFree(b->d_err);
     delete b;
     return XE_ERR_NOMEM;
@@ -640,6 +695,9 @@ XE_API xe_status xe_beam_destroy(xe_beam_t b) {
   cudaDeviceSynchronize();
   cudaFree(b->d_wt);
   cudaFree(b->d_bias);
+  cudaFree(b->d_wa);
+  cudaFree(b->d_sigma);
+  cudaFree(b->d_osc);
   cudaFree(b->d_err);
   delete b;
   return XE_OK;
@@ -648,8 +706,12 @@ XE_API xe_status xe_beam_destroy(xe_beam_t b) {
 XE_API xe_status xe_beam_set_weights(xe_beam_t b, const float* d_w, void* stream) {
   if (!b || !d_w) return XE_ERR_INVALID_ARG;
   if (!aligned_to(d_w, 8)) return XE_ERR_ALIGNMENT;
-  if (xe::launch_beam_weights(d_w, b->N, b->C, b->B, b->S, b->d_wt, b->d_bias, static_cast<cudaStream_t>(stream)) !=
-      cudaSuccess) {
+  const cudaError_t e =
+      b->t_on_n ? xe::launch_beam8_weights(d_w, b->N, b->C, b->B, b->S8, b->d_wa, b->d_sigma, b->d_osc, b->d_bias,
+                                           static_cast<cudaStream_t>(stream))
+                : xe::launch_beam_weights(d_w, b->N, b->C, b->B, b->S, b->d_wt, b->d_bias,
+                                          static_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) {
     b->last_error = "weight conversion launch failed";
     return XE_ERR_CUDA;
   }
@@ -662,6 +724,7 @@ XE_API xe_status xe_beam_form(xe_beam_t b, const uint8_t* d_gulp, int ntime, flo
   if (ntime == 0) return XE_OK;
   if (!d_gulp || !d_out) return XE_ERR_INVALID_ARG;
   if (!aligned_to(d_gulp, 16) || !aligned_to(d_out, 16)) return XE_ERR_ALIGNMENT;
+  if (b->t_on_n) return form_t_on_n(b, d_gulp, ntime, d_out, static_cast<cudaStream_t>(stream));
   CUtensorMap map;
   const bool map4 = b->N % 64 == 0;   // whole 64-input chunks: one copy per 4 stages
   bool enc;

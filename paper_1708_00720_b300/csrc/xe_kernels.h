@@ -91,4 +91,27 @@ int beam_w_group(int B);   // stages of weights per bulk copy
 cudaError_t launch_beam_weights(const float* w, int N, int C, int B, int S, uint16_t* wt, float* bias,
                                 cudaStream_t stream);
 
+// Beamformer with time along the MMA's N (xe_beam8.cu), for B <= 16 beams
+// and N <= 512 inputs: operand A = the weights as four e4m3 terms per
+// float16 coefficient in tensor memory, operand B = the voltages as biased
+// e4m3 bytes.  The raw map views the gulp as uint8 {N, C, T} with box
+// {128, 1, 128} and the 128-byte swizzle.
+struct Beam8Params {
+  int N, C, B;            // inputs, channels, beams
+  int S;                  // 128-input stages, ceil(N / 128) (<= 4)
+  int T;                  // samples in this launch
+  int tiles;              // 128-sample time tiles, ceil(T / 128)
+  const uint8_t* wa;      // [C][128 rows][256 S] e4m3 operand-A images (row 32 q + 8 k + m: term k of output 8 q + m)
+  const float* osc;       // [C] 2^9 / sigma_c
+  const float* bias;      // [C][32] 8 * (sum of each output row's coefficients)
+  float* out;             // [T][C][B] complex64
+  int* err;               // device error word
+  unsigned long long timeout_ns;
+};
+int beam8_smem_bytes();
+cudaError_t launch_beam8(const CUtensorMap* tmap, const Beam8Params& prm, int grid, cudaStream_t stream);
+// Weights [C][B][N] complex64 -> sigma [C], osc [C], bias [C][32] and the A images.
+cudaError_t launch_beam8_weights(const float* w, int N, int C, int B, int S, uint8_t* wa, float* sigma, float* osc,
+                                 float* bias, cudaStream_t stream);
+
 }  // namespace xe
