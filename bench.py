@@ -550,7 +550,7 @@ def run_beam(args, world, rank, local, pg, dev):
         line = {
             "metric": BEAM_METRIC, "value": value, "unit": "cMAC TOPS", "n_gpus": world,
             "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": ms,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f16 x biased-f16 -> f32",
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "e4m3 (float16 weights as 4 exact e4m3 terms) x biased e4m3 -> f32",
             "data": "synthetic (seeded 4+4-bit Gaussian sigma=2, phase-only steering weights)",
             "config": {"workload": WORKLOADS["beam"][1], "n_input": N, "n_chan": C, "ntime": T, "n_beam": B,
                        "l2": f"gulp ({x.nbytes >> 20} MiB) exceeds L2 (126 MB); no flush",
