@@ -89,6 +89,23 @@ def test_random_weights_and_uniform_bytes(bm):
     check(run(bm, x, w, B), x, w)
 
 
+def test_weight_dynamic_range(bm):
+    """Weights of one channel spanning 2^-20 .. 1 in magnitude (below 2^-18 of
+    the largest the time-along-N kernel's e4m3 terms are no longer exact, and
+    err by less than 2^-28 of it), a channel of zero weights and one of large
+    weights (~1e4); 8 beams, so half of that kernel's operand rows are zero."""
+    N, C, B, T = 256, 3, 8, 384
+    rng = np.random.default_rng(12)
+    mag = 2.0 ** rng.uniform(-20, 0, (C, B, N))
+    w = (mag * np.exp(2j * np.pi * rng.random((C, B, N)))).astype(np.complex64)
+    w[1] = 0
+    w[2] *= np.float32(1.0e4)
+    x = synth.voltages(N, C, T, seed=12, random_phase=True)
+    got = run(bm, x, w, B)
+    assert np.all(got[:, 1] == 0)
+    check(got, x, w)
+
+
 def test_extreme_samples(bm):
     N, C, B, T = 128, 2, 8, 256
     x = np.full((T, C, N), 0x88, np.uint8)            # -8 - 8i everywhere
