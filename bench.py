@@ -733,9 +733,11 @@ def run_ours(args):
     vis = eng.vis_empty(device=dev)
     stream = torch.cuda.current_stream(dev)
 
+    # One step = one integration of one gulp (the workload's integration
+    # length): correlate, integrate and emit the ci32 visibilities, fused
+    # into one xe_correlate_emit call (the kernels write the caller's buffer).
     def step():
-        eng.correlate(gulp, stream=stream)
-        eng.integrate(vis, stream=stream)
+        eng.correlate_emit(gulp, vis, stream=stream)
 
     for _ in range(max(args.warmup, 3)):
         step()
@@ -754,9 +756,8 @@ def run_ours(args):
         t_start.record(stream)
         for k in range(args.steps):
             ev[k][0].record(stream)
-            eng.correlate(gulp, stream=stream)
+            eng.correlate_emit(gulp, vis, stream=stream)
             ev[k][1].record(stream)
-            eng.integrate(vis, stream=stream)
             ev[k][2].record(stream)
         t_end.record(stream)
         torch.cuda.synchronize(dev)
@@ -777,14 +778,13 @@ def run_ours(args):
     if args.operand != "int32" and not args.skip_int32:
         e32 = xe.XEngine(N, C, T, "int32", "ci32")
         for _ in range(2):
-            e32.correlate(gulp, stream=stream)
+            e32.correlate_emit(gulp, vis, stream=stream)
         torch.cuda.synchronize(dev)
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         n32 = 3
         a.record(stream)
         for _ in range(n32):
-            e32.correlate(gulp, stream=stream)
-            e32.integrate(vis, stream=stream)
+            e32.correlate_emit(gulp, vis, stream=stream)
         b.record(stream)
         torch.cuda.synchronize(dev)
         e32.check()

@@ -145,6 +145,19 @@ XE_API xe_status xe_correlate(xe_plan_t plan, const uint8_t *d_gulp, int ntime,
  * type = the plan's xe_out).  d_vis must be 8-byte aligned. */
 XE_API xe_status xe_integrate(xe_plan_t plan, void *d_vis, void *stream);
 
+/* A one-gulp integration in one call (sections "Some included blocks" and
+ * "Memory management and ring buffers": correlate, accumulate and emit when
+ * the integration is a single gulp): the visibilities of this gulp alone,
+ * written by the correlation kernels straight into d_vis, the same values
+ * as xe_reset + xe_correlate (accumulate 0) + xe_integrate but without the
+ * copy out of the plan's accumulator.  The plan's accumulator and sample
+ * count are left untouched.  ci32 plans only (XE_ERR_INVALID_ARG for cf32);
+ * d_vis int32 [C][N(N+1)/2][2], 8-byte aligned, caller-owned; d_gulp as for
+ * xe_correlate (ntime = 0 zeroes d_vis).  Errors as for xe_correlate.
+ * Asynchronous on stream. */
+XE_API xe_status xe_correlate_emit(xe_plan_t plan, const uint8_t *d_gulp, int ntime, void *d_vis,
+                                   void *stream);
+
 /* Zero the accumulator and the sample counter. */
 XE_API xe_status xe_reset(xe_plan_t plan, void *stream);
 

@@ -127,19 +127,21 @@ bool xe::encode_tensor_u8(CUtensorMap* map, const void* base, int rank, const un
 
 namespace {
 
-// Enqueue the correlation of one gulp (already validated) on `stream`.
+// Enqueue the correlation of one gulp (already validated) on `stream` into
+// the int32 accumulator `acc` ([C][N(N+1)/2][2]): the plan's own, or the
+// caller's visibility buffer for a one-gulp integration.
 xe_status enqueue_correlate(xe_plan* p, const uint8_t* d_gulp, int ntime, int accumulate,
-                            cudaStream_t stream) {
+                            cudaStream_t stream, int32_t* acc) {
   if (ntime == 0) {
     if (!accumulate) {
-      cudaError_t e = cudaMemsetAsync(p->d_acc, 0, static_cast<size_t>(p->n_pairs) * 8, stream);
+      cudaError_t e = cudaMemsetAsync(acc, 0, static_cast<size_t>(p->n_pairs) * 8, stream);
       if (e != cudaSuccess) return cuda_fail(p, e, "cudaMemsetAsync");
     }
     return XE_OK;
   }
   const size_t row_bytes = static_cast<size_t>(p->C) * static_cast<size_t>(p->N);
   if (p->op == XE_OPERAND_INT32_CUDACORE) {
-    cudaError_t e = xe::launch_xcorr_cudacore(d_gulp, ntime, p->C, p->N, p->d_acc, accumulate, stream);
+    cudaError_t e = xe::launch_xcorr_cudacore(d_gulp, ntime, p->C, p->N, acc, accumulate, stream);
     if (e != cudaSuccess) return cuda_fail(p, e, "cudacore launch");
     ++p->launches;
     return XE_OK;
@@ -161,7 +163,7 @@ xe_status enqueue_correlate(xe_plan* p, const uint8_t* d_gulp, int ntime, int ac
     prm.units = 0;  // set by the launcher
     prm.nks = static_cast<int>((T + rows - 1) / rows * (rows / 32));   // whole stages of 32-sample steps
     prm.accumulate = (accumulate || t0 > 0) ? 1 : 0;
-    prm.acc = p->d_acc;
+    prm.acc = acc;
     prm.err = p->d_err;
     prm.timeout_ns = kWaitTimeoutNs;
     prm.split_ws = p->d_split;
@@ -309,10 +311,21 @@ xe_status xe_correlate(xe_plan_t p, const uint8_t* d_gulp, int ntime, int accumu
   xe_status st = check_correlate(p, d_gulp, ntime, accumulate);
   if (st != XE_OK) return st;
   if (ntime > 0 && !aligned16(d_gulp)) return XE_ERR_ALIGNMENT;
-  st = enqueue_correlate(p, d_gulp, ntime, accumulate, static_cast<cudaStream_t>(stream));
+  st = enqueue_correlate(p, d_gulp, ntime, accumulate, static_cast<cudaStream_t>(stream), p->d_acc);
   if (st != XE_OK) return st;
   p->samples = (accumulate ? p->samples : 0) + ntime;
   return XE_OK;
+}
+
+xe_status xe_correlate_emit(xe_plan_t p, const uint8_t* d_gulp, int ntime, void* d_vis, void* stream) {
+  if (!p || !d_vis) return XE_ERR_INVALID_ARG;
+  if (p->out_type != XE_OUT_CI32) return XE_ERR_INVALID_ARG;
+  if (ntime < 0 || ntime > p->max_ntime) return ntime < 0 ? XE_ERR_INVALID_ARG : XE_ERR_SHAPE;
+  if (!d_gulp && ntime > 0) return XE_ERR_INVALID_ARG;
+  if (ntime > integration_bound(p)) return XE_ERR_ACCUM_BOUND;
+  if ((reinterpret_cast<uintptr_t>(d_vis) & 7u) != 0) return XE_ERR_ALIGNMENT;
+  if (ntime > 0 && !aligned16(d_gulp)) return XE_ERR_ALIGNMENT;
+  return enqueue_correlate(p, d_gulp, ntime, 0, static_cast<cudaStream_t>(stream), static_cast<int32_t*>(d_vis));
 }
 
 xe_status xe_integrate(xe_plan_t p, void* d_vis, void* stream) {
@@ -414,11 +427,11 @@ xe_status xe_correlate_host(xe_plan_t p, const uint8_t* h_gulp, int ntime, int a
     cudaEventRecord(ev, p->s_copy);
     cudaStreamWaitEvent(p->s_comp, ev, 0);
     cudaEventDestroy(ev);
-    st = enqueue_correlate(p, p->d_stage + off, T, (accumulate || t0 > 0) ? 1 : 0, p->s_comp);
+    st = enqueue_correlate(p, p->d_stage + off, T, (accumulate || t0 > 0) ? 1 : 0, p->s_comp, p->d_acc);
     if (st != XE_OK) return st;
   }
   if (ntime == 0) {
-    st = enqueue_correlate(p, p->d_stage, 0, accumulate, p->s_comp);
+    st = enqueue_correlate(p, p->d_stage, 0, accumulate, p->s_comp, p->d_acc);
     if (st != XE_OK) return st;
   }
   const size_t out_bytes = static_cast<size_t>(p->n_pairs) * 8;

@@ -63,6 +63,7 @@ def _load() -> ctypes.CDLL:
         "xe_unpack": ([P, P, P, I, P], I),
         "xe_correlate": ([P, P, I, I, P], I),
         "xe_integrate": ([P, P, P], I),
+        "xe_correlate_emit": ([P, P, I, P, P], I),
         "xe_reset": ([P, P], I),
         "xe_samples_integrated": ([P, ctypes.POINTER(LL)], I),
         "xe_correlate_host": ([P, P, I, I, P], I),
@@ -162,6 +163,11 @@ def xe_integrate(plan, d_vis, stream=None) -> None:
     _check(_lib.xe_integrate(plan, _ptr(d_vis), _stream(stream)), "xe_integrate", plan)
 
 
+def xe_correlate_emit(plan, d_gulp, ntime: int, d_vis, stream=None) -> None:
+    _check(_lib.xe_correlate_emit(plan, _ptr(d_gulp), ntime, _ptr(d_vis), _stream(stream)),
+           "xe_correlate_emit", plan)
+
+
 def xe_reset(plan, stream=None) -> None:
     _check(_lib.xe_reset(plan, _stream(stream)), "xe_reset", plan)
 
@@ -225,6 +231,18 @@ class XEngine:
         if out is None:
             out = self.vis_empty(device="cuda")
         xe_integrate(self.plan, out, stream)
+        return out
+
+    def correlate_emit(self, gulp, out=None, stream=None):
+        """Visibilities of this gulp alone, written straight into `out`
+        (ci32 plans); the plan's accumulator is not touched."""
+        if gulp.dtype != self._torch.uint8 or gulp.dim() != 3 or not gulp.is_contiguous():
+            raise ValueError("gulp must be a contiguous uint8 tensor [T][C][N]")
+        if gulp.shape[1] != self.n_chan or gulp.shape[2] != self.n_input:
+            raise ValueError("gulp shape does not match the plan")
+        if out is None:
+            out = self.vis_empty(device="cuda")
+        xe_correlate_emit(self.plan, gulp, gulp.shape[0], out, stream)
         return out
 
     def reset(self, stream=None) -> None:

@@ -146,6 +146,47 @@ def test_time_sliced_leftover_units(xe, operand, shape):
 
 
 @pytest.mark.parametrize("operand", OPS)
+def test_correlate_emit(xe, operand):
+    """A one-gulp integration written straight into the caller's buffer: the
+    values of correlate + integrate, the buffer overwritten (not added to),
+    the plan's own accumulator and sample count untouched."""
+    import torch
+    N, C, T = 272, 25, 2048      # leftover units cut along time on the tensor-core paths
+    x, ref = _split_case((N, C, T))
+    eng = xe.XEngine(N, C, T, operand)
+    g = torch.from_numpy(x).cuda()
+    eng.correlate(g[:100])
+    before = eng.integrate().cpu().numpy()
+    out = torch.full((C, eng.n_baselines, 2), 7, dtype=torch.int32, device="cuda")
+    assert eng.correlate_emit(g, out) is out
+    eng.check()
+    np.testing.assert_array_equal(out.cpu().numpy(), ref)
+    np.testing.assert_array_equal(eng.integrate().cpu().numpy(), before)
+    assert eng.samples() == 100
+    eng.correlate_emit(g[:0], out)                   # an empty gulp: zero visibilities
+    assert (out.cpu().numpy() == 0).all()
+    eng.close()
+    with pytest.raises(xe.XEngineError) as e:        # ci32 plans only
+        f = xe.XEngine(N, C, T, operand, "cf32")
+        try:
+            f.correlate_emit(g, torch.empty((C, eng.n_baselines, 2), dtype=torch.int32, device="cuda"))
+        finally:
+            f.close()
+    assert e.value.status == xe.XE_ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("operand", ["fp8", "fp16"])
+def test_correlate_emit_longer_than_one_launch(xe, operand):
+    import torch
+    x = synth.voltages(32, 2, 40000, seed=3)
+    eng = xe.XEngine(32, 2, 40000, operand)
+    out = eng.correlate_emit(torch.from_numpy(x).cuda())
+    eng.check()
+    np.testing.assert_array_equal(out.cpu().numpy(), oracle.correlate(x))
+    eng.close()
+
+
+@pytest.mark.parametrize("operand", OPS)
 def test_accumulate_and_reset(xe, operand):
     import torch
     x = synth.voltages(144, 3, 500, seed=9, random_phase=True)
