@@ -40,7 +40,10 @@
  *  - Calls never throw and never abort; they return an xe_status.  After
  *    XE_ERR_CUDA, xe_plan_last_error() holds the CUDA error text.
  *  - A plan is not thread-safe: calls on one plan must be serialised by the
- *    caller.  Different plans are independent.
+ *    caller, and their device work must not overlap (use one stream per
+ *    plan, or order the streams): the correlation kernels of a plan share
+ *    its accumulator and its scratch, also for xe_correlate_emit.
+ *    Different plans are independent.
  */
 #ifndef XENGINE_H
 #define XENGINE_H
