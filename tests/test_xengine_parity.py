@@ -28,16 +28,21 @@ def xe():
     return xengine
 
 
-def run(xe, x, operand, out="ci32", max_ntime=None):
+def run(xe, x, operand, out="ci32", max_ntime=None, emit=False):
+    """Visibilities of one gulp through correlate + integrate, or (emit) through
+    the fused one-gulp call the benchmark step times."""
     import torch
     T, C, N = x.shape
     eng = xe.XEngine(N, C, max_ntime or max(T, 1), operand, out)
     g = torch.from_numpy(np.ascontiguousarray(x)).cuda()
-    eng.correlate(g)
-    v = eng.integrate()
+    if emit:
+        v = eng.correlate_emit(g)
+    else:
+        eng.correlate(g)
+        v = eng.integrate()
     torch.cuda.synchronize()
     eng.check()
-    assert eng.samples() == T
+    assert eng.samples() == (0 if emit else T)
     res = v.cpu().numpy()
     eng.close()
     if out == "cf32":
@@ -317,8 +322,11 @@ def properties_check(v, x):
 
 @pytest.mark.parametrize("operand", ["fp8", "int32"])
 def test_lwa_workload_sampled(xe, operand):
+    """512 inputs, 256 channels, 8192 samples in the benchmark's launch
+    configuration (the fused one-gulp call), equal to correlate + integrate."""
     x = synth.config_voltages("lwa")
-    v = run(xe, x, operand)
+    v = run(xe, x, operand, emit=True)
+    np.testing.assert_array_equal(v, run(xe, x, operand))
     properties_check(v, x)
     sampled_check(v, x, np.random.default_rng(1))
     # autocorrelations of a few channels in full
@@ -330,7 +338,8 @@ def test_lwa_workload_sampled(xe, operand):
 @pytest.mark.parametrize("operand", ["fp8", "fp16"])
 def test_large_n_workload_sampled(xe, operand):
     x = synth.config_voltages("large_n")
-    v = run(xe, x, operand)
+    v = run(xe, x, operand, emit=True)
+    np.testing.assert_array_equal(v, run(xe, x, operand))
     properties_check(v, x)
     sampled_check(v, x, np.random.default_rng(2))
 
