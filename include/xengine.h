@@ -361,9 +361,13 @@ XE_API xe_status xe_wait_flag(const int *d_flag, int expected, long long timeout
  * on the 4+4-bit samples):  y[t][c][b] = sum_i w[c][b][i] x[t][c][i].
  *
  * d_w: complex64 (interleaved float pairs) weights [n_chan][n_beam][n_input]
- * in device memory; xe_beam_set_weights converts them to float16 operand
- * tiles (real and imaginary parts rounded to float16: the operand precision)
- * and per-column bias sums held by the object.  xe_beam_form reads a gulp
+ * in device memory; xe_beam_set_weights rounds their real and imaginary
+ * parts to float16 (the operand precision) and converts them into the
+ * kernel's operand form, held by the object with per-output bias sums: for
+ * n_beam <= 16 and n_input <= 512, four e4m3 terms per coefficient after a
+ * per-channel power-of-two scale (exact for every coefficient of at least
+ * 2^-18 of the channel's largest; others err by less than 2^-28 of it),
+ * otherwise float16 tiles.  xe_beam_form reads a gulp
  * uint8[ntime][n_chan][n_input] (same layout as xe_correlate) and writes
  * d_out complex64 [ntime][n_chan][n_beam]; products are accumulated in
  * float32 on the tensor cores.  n_beam in 8..64, a multiple of 8; n_input

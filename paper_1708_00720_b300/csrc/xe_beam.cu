@@ -3,6 +3,10 @@
 // on the 4+4-bit samples):
 //   y[t][c][b] = sum_i w[c][b][i] x[t][c][i]
 //
+// This file holds the beamformer's C ABI, which sends up to 16 beams over up
+// to 512 inputs to the time-along-N kernel of xe_beam8.cu, and the
+// time-along-M kernel below for every other shape.
+//
 // Per channel this is a complex matrix product Y (T x B) = X (T x N) W^T,
 // written as one real product on the tcgen05 tensor cores (kind::f16):
 //   [Y_re | Y_im] = [X_re | X_im] . [[ W_re,  W_im],
