@@ -251,9 +251,15 @@ beam8_kernel(const __grid_constant__ CUtensorMap tmap, const Beam8Params p) {
   } else if (warp == kMmaWarp) {
     // ------------------------------------------------------------ MMA issuer
     if (lane == 0) {
-      // e4m3 x e4m3 -> f32, A from tensor memory, B K-major; M = 128, N = 128
+      // e4m3 x e4m3 -> f32, A from tensor memory, B K-major; M = 128, N = 128.
+      // Descriptors are one base per operand slot plus compile-time offsets
+      // and the slot and its phase are counters: the tensor core's
+      // instruction queue is short, so scalar work between MMAs shows.
       constexpr uint32_t idesc = (1u << 4) | ((128u >> 3) << 17) | ((128u >> 4) << 24);
-      int h = 0, j = 0, wl = 0;
+      constexpr uint32_t kSlotDesc = kOpStage >> 4, kAtomDesc = kAtom >> 4;   // descriptor address units
+      const uint64_t desc0 = sdesc_k_sw128(smem_u32(s.op));
+      int j = 0, wl = 0, os = 0;
+      uint32_t oph = 0;                     // phase of operand slot os
       int prev_c = -1;
       bool ok = true;
       for (long long u = u0; u < u1 && ok; ++u, ++j) {
@@ -273,22 +279,27 @@ beam8_kernel(const __grid_constant__ CUtensorMap tmap, const Beam8Params p) {
         }
         tc_fence_after();
         const uint32_t d = tmem + kD0 + 128 * ab;
-        for (int st = 0; st < S; ++st, ++h) {
-          const int os = h % kOp;
-          if (!wait_or_abort(&s.op_full[os], (h / kOp) & 1, lim, abort_flag)) {
+        for (int st = 0; st < S; ++st) {
+          if (!wait_or_abort(&s.op_full[os], oph, lim, abort_flag)) {
             if (!*abort_flag) fail(s, p.err, kErrOpFull);
             ok = false;
             break;
           }
           tc_fence_after();
-          const uint32_t b0 = smem_u32(s.op + os * kOpStage);
+          const uint64_t bd = desc0 + static_cast<uint64_t>(kSlotDesc * os);
+          const uint32_t a0 = tmem + 64 * st;
+          const uint32_t acc_first = st > 0 ? 1u : 0u;
 #pragma unroll
           for (int a = 0; a < 2; ++a)
 #pragma unroll
             for (int ks = 0; ks < 4; ++ks)
-              mma_f8_tmem_a(d, tmem + 64 * st + 32 * a + 8 * ks, sdesc_k_sw128(b0 + a * kAtom + 32 * ks), idesc,
-                            (st | a | ks) != 0 ? 1u : 0u);
+              mma_f8_tmem_a(d, a0 + 32 * a + 8 * ks, bd + kAtomDesc * a + 2 * ks, idesc,
+                            (a | ks) != 0 ? 1u : acc_first);
           mma_commit(&s.op_empty[os]);
+          if (++os == kOp) {
+            os = 0;
+            oph ^= 1u;
+          }
         }
         if (!ok) break;
         mma_commit(&s.acc_full[ab]);

@@ -640,12 +640,19 @@ xcorr_tc8_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant
     }
   } else if (warp == 1) {
     // ====================================================== MMA issuer (CTA 0)
+    // The tensor core's instruction queue is short, so the issuing thread's
+    // scalar work between MMAs shows: descriptors are one base per operand
+    // slot plus compile-time offsets, and the slot and its phase are
+    // counters (a probe: 79 -> 69 cycles per MMA).
     if (lane == 0) {
-      int sit = 0, ui = 0;
+      int ui = 0, st = 0;
+      uint32_t ph = 0;                            // phase of operand slot st
       bool ok = true;
       // A from tensor memory, B K-major; e4m3 x e4m3 or f16 x f16 -> f32, M = 256 (pair), N = 128
       constexpr uint32_t id_pos = (1u << 4) | ((128u >> 3) << 17) | ((256u >> 4) << 24);
       constexpr uint32_t id_neg = id_pos | (1u << 14);
+      constexpr uint32_t kSlotDesc = kOpStage >> 4, kPlaneDesc = kPlane >> 4;   // descriptor address units
+      const uint64_t desc0 = sdesc_k_sw128(smem_u32(s.op));
       const uint32_t d_re = tmem, d_im = tmem + 128;
       for (int it = 0; it < s.sched[0] && ok; ++it, ++ui) {
         const Item w = item_at(s.sched, it);
@@ -654,24 +661,23 @@ xcorr_tc8_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant
           break;
         }
         tc_fence_after();
-        for (int ks = w.k0; ks < w.k1; ks += G::kSteps, ++sit) {
-          const int st = sit % kOpStages;
-          if (!wait_or_abort(&s.op_full[st], (sit / kOpStages) & 1, lim, abort_flag)) {
+        for (int ks = w.k0; ks < w.k1; ks += G::kSteps) {
+          if (!wait_or_abort(&s.op_full[st], ph, lim, abort_flag)) {
             fail(s, prm.err, kErrWaitOpFull);
             ok = false;
             break;
           }
           tc_fence_after();
           const uint32_t a0 = tmem + kTmemA0 + kTmemAStage * st;
-          const uint32_t op = smem_u32(s.op + st * kOpStage);
+          const uint64_t bd = desc0 + static_cast<uint64_t>(kSlotDesc * st);
+          const uint32_t acc_first = ks == w.k0 ? 0u : 1u;   // the unit's (or part's) first stage overwrites D
           if constexpr (EB == 1) {
             // per step: A columns re 8 | im 8, B K bytes 32
 #pragma unroll
             for (int sub = 0; sub < G::kSteps; ++sub) {
               const uint32_t a_re = a0 + 16 * sub, a_im = a_re + 8;
-              const uint64_t b_re = sdesc_k_sw128(op + 32 * sub);
-              const uint64_t b_im = sdesc_k_sw128(op + kPlane + 32 * sub);
-              const uint32_t acc0 = (ks - w.k0 + sub) > 0 ? 1u : 0u;
+              const uint64_t b_re = bd + 2 * sub, b_im = bd + kPlaneDesc + 2 * sub;
+              const uint32_t acc0 = sub > 0 ? 1u : acc_first;
               mma2_f8_tmem_a(d_re, a_re, b_re, id_pos, acc0);
               mma2_f8_tmem_a(d_re, a_im, b_im, id_pos, 1u);
               mma2_f8_tmem_a(d_im, a_im, b_re, id_pos, acc0);
@@ -685,9 +691,8 @@ xcorr_tc8_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant
 #pragma unroll
               for (int kk = 0; kk < 2; ++kk) {
                 const uint32_t a_re = a0 + 32 * sub + 8 * kk, a_im = a_re + 16;
-                const uint64_t b_re = sdesc_k_sw128(op + 64 * sub + 32 * kk);
-                const uint64_t b_im = sdesc_k_sw128(op + kPlane + 64 * sub + 32 * kk);
-                const uint32_t acc0 = (ks - w.k0 + sub + kk) > 0 ? 1u : 0u;
+                const uint64_t b_re = bd + 4 * sub + 2 * kk, b_im = bd + kPlaneDesc + 4 * sub + 2 * kk;
+                const uint32_t acc0 = (sub + kk) > 0 ? 1u : acc_first;
                 mma2_f16_tmem_a(d_re, a_re, b_re, id_pos, acc0);
                 mma2_f16_tmem_a(d_re, a_im, b_im, id_pos, 1u);
                 mma2_f16_tmem_a(d_im, a_im, b_re, id_pos, acc0);
@@ -695,6 +700,10 @@ xcorr_tc8_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant
               }
           }
           commit2(&s.op_empty[st]);
+          if (++st == kOpStages) {
+            st = 0;
+            ph ^= 1u;
+          }
         }
         if (!ok) break;
         commit2(s.acc_full);
