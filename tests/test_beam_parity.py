@@ -70,6 +70,8 @@ SHAPES = [  # (N, C, B, T): input padding, time tails, every beam count, multi-s
     (16, 1, 24, 1),
     (1024, 2, 16, 256),   # weights too large to stay resident: streamed per group of stages
     (256, 40, 16, 128),   # many channels per CTA: resident weights reloaded at channel changes
+    (400, 3, 16, 200),    # time along N: a partial last 128-input stage (zero-filled inputs)
+    (512, 2, 16, 1),      # time along N: one sample per channel
 ]
 
 
