@@ -26,7 +26,9 @@
 // by J column two at a time; the odd one out of a column, (nt-1, j), is
 // computed as its transpose (I = j, J = nt-1) next to the last diagonal tile
 // and written back conjugated and transposed.  If the count is still odd,
-// CTA 1 repeats its partner's tile and writes nothing.
+// CTA 1 repeats its partner's tile and writes nothing.  Units left over after
+// the last full round of clusters are cut along time (see "schedule" below)
+// and their slices summed by split_combine_kernel.
 //
 // Both operand widths share the design (template parameter EB): a stage is
 // 128 K bytes per operand row, i.e. 4 steps of 32 samples as e4m3 (one
