@@ -272,10 +272,12 @@ __device__ __forceinline__ void tma_prefetch_3d(const void* desc, int x, int y, 
                ::"l"(reinterpret_cast<uint64_t>(desc)), "r"(x), "r"(y), "r"(z)
                : "memory");
 }
-// The raw-tile producers prefetch the tiles kPrefetch stages ahead into L2,
-// so a copy waits for L2 rather than DRAM (e4m3 lwa: 1.035 -> 0.961 ms; 4 and
-// 8 stages ahead, or prefetching into the next unit, measured no better).
-constexpr int kPrefetch = 2;
+// The raw-tile producers prefetch the tile kPrefetch stages ahead into L2,
+// so a copy waits for L2 rather than DRAM (e4m3 lwa: 1.035 -> 0.961 ms at two
+// stages ahead; with the leaner MMA issue loop one stage ahead is a little
+// better, 0.914 -> 0.907 ms; three, four or eight stages ahead, or
+// prefetching into the next unit, measured no better).
+constexpr int kPrefetch = 1;
 // K-major operand, 128-byte swizzle: 8-row groups 1024 B apart.
 __device__ __forceinline__ uint64_t sdesc_k_sw128(uint32_t saddr) {
   uint64_t d = 0;
