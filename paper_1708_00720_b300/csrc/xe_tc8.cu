@@ -55,8 +55,10 @@
 //                               D_im += A_im B_re^T - A_re B_im^T
 //    (negate-B bit); commits are multicast to both CTAs.
 //  * Epilogue (each CTA): D (single buffer, 256 TMEM columns) is copied out
-//    per 32-column chunk (three chunks to shared staging, one to registers)
-//    and released to the MMA; then the bias is removed exactly from per-input
+//    per 32-column chunk (three chunks to shared staging, one to registers),
+//    D_re first and then D_im, each half released to the MMA as soon as it
+//    is read (the next unit's real-part MMAs of its first stages run while
+//    D_im is still being read); then the bias is removed exactly from per-input
 //    sums of u (the column sums of the other half of J are read from the
 //    partner's shared memory) and rows are written coalesced to the
 //    accumulator:
@@ -100,11 +102,13 @@ constexpr int kPlane = kHalf * 128;             // 8 KB: 64 rows x 128 K bytes, 
 constexpr int kOpStage = 2 * kPlane;            // re plane, im plane
 constexpr int kOpBytes = kOpStages * kOpStage;
 constexpr int kStageBufs = 3;                   // accumulator chunks staged per epilogue warp
-constexpr int kStageBytes = 4 * kStageBufs * 32 * 32 * 8;  // per warp and chunk: 32 rows x 32 int2
+constexpr int kStageRow = 33;                   // words per staged row (padded: conflict-free both ways)
+constexpr int kStageChunk = 32 * kStageRow;     // one 32 x 32 chunk of one half (re or im)
+constexpr int kStageBytes = 4 * 2 * kStageBufs * kStageChunk * 4;  // per warp: re chunks, then im chunks
 constexpr int kSlotInts = 2 * kTile + 2 * kHalf;  // P_I, Q_I (128 each), P_J, Q_J of this CTA's half
 constexpr int kSumsBytes = 2 * kSlotInts * 4 + 2 * kTile * 4 + 2 * kTile * 4;
 // 2 slots of sums, column corrections (re, im), row and column triangle offsets
-constexpr int kNumBars = 2 * kRawStages + 2 * kOpStages + 2 + 2 + 2 + 1;
+constexpr int kNumBars = 2 * kRawStages + 2 * kOpStages + 3 + 2 + 2 + 1;
 constexpr int kCtlBytes = 64;   // after the barriers: TMEM address, abort flag, schedule
 
 // Operand width EB (1: e4m3, 2: f16) sets the samples per stage and the raw tiles.
@@ -151,13 +155,13 @@ enum ErrCode : int {
 struct Smem {
   uint8_t* op;     // [kOpStages][re, im][64 rows x 128 K bytes]  B planes (this CTA's half)
   uint8_t* raw;    // [kRawStages][I: kRawTile | J half: kRawHalf]  (Geo<EB>)
-  int2* stage;     // [4 warps][kStageBufs][32 rows][32], column index XOR row
+  int* stage;      // [4 warps][re, im][kStageBufs][32 rows][kStageRow]
   int* sums;       // [2][kSlotInts]
   float* colcorr;  // [2][128]: per-column bias corrections of the current unit (re, im)
   int* rowoff;     // [128]: packed-triangle offset i (i + 1) / 2 of each accumulator row's input i
   int* coloff;     // [128]: the same for each accumulator column's input j
   uint64_t *raw_full, *raw_empty, *op_full, *op_empty;
-  uint64_t *acc_full, *acc_empty, *sums_full, *sums_empty, *final_bar;
+  uint64_t *acc_full, *acc_empty, *acc_empty_im, *sums_full, *sums_empty, *final_bar;
   uint32_t* tmem_slot;
   int* abort_flag;
   int* sched;      // schedule header and tail items (item_at)
@@ -169,7 +173,7 @@ __device__ __forceinline__ Smem carve(uint8_t* base) {
   Smem p;
   p.op = base;
   p.raw = base + kOpBytes;
-  p.stage = reinterpret_cast<int2*>(base + kOpBytes + G::kRawBytes);
+  p.stage = reinterpret_cast<int*>(base + kOpBytes + G::kRawBytes);
   p.sums = reinterpret_cast<int*>(base + kOpBytes + G::kRawBytes + kStageBytes);
   p.colcorr = reinterpret_cast<float*>(p.sums + 2 * kSlotInts);
   p.rowoff = reinterpret_cast<int*>(p.colcorr + 2 * kTile);
@@ -181,6 +185,7 @@ __device__ __forceinline__ Smem carve(uint8_t* base) {
   p.op_empty = b; b += kOpStages;
   p.acc_full = b; b += 1;
   p.acc_empty = b; b += 1;
+  p.acc_empty_im = b; b += 1;
   p.sums_full = b; b += 2;
   p.sums_empty = b; b += 2;
   p.final_bar = b; b += 1;
@@ -512,12 +517,69 @@ struct PairSums {
   }
 };
 
-// One 32-column chunk of this lane's accumulator row, as raw float32 bits,
-// into a staging buffer (row `lane`, column index XOR lane): the quickest way
+// One 32-column chunk of one half (re or im) of this lane's accumulator row,
+// as raw float32 bits, into row `lane` of a staging chunk: the quickest way
 // to get D out of tensor memory.  The bias is removed after D is released.
-__device__ __forceinline__ void stage_raw(int2* buf, const uint32_t (&vre)[32], const uint32_t (&vim)[32], int lane) {
+// Rows of 33 words keep both the row-wise stores here and the column-wise
+// reads of the write-out free of bank conflicts, with immediate offsets.
+__device__ __forceinline__ void stage_raw(int* buf, const uint32_t (&v)[32], int lane) {
+  int* w = buf + lane * kStageRow;
 #pragma unroll
-  for (int k = 0; k < 32; ++k) buf[lane * 32 + (k ^ lane)] = make_int2(static_cast<int>(vre[k]), static_cast<int>(vim[k]));
+  for (int k = 0; k < 32; ++k) w[k] = static_cast<int>(v[k]);
+}
+
+// Staged value (row r, column k) of a chunk: real part, imaginary part.
+__device__ __forceinline__ int2 staged(const int* chunk, int r, int k) {
+  return make_int2(chunk[r * kStageRow + k], chunk[kStageBufs * kStageChunk + r * kStageRow + k]);
+}
+
+// The MMAs of one operand stage for the real half of D (WHICH & 1) and/or its
+// imaginary half (WHICH & 2):
+//   D_re += A_re B_re^T + A_im B_im^T,   D_im += A_im B_re^T - A_re B_im^T.
+// A from tensor memory (stage columns at a0), B K-major in shared memory
+// (descriptor bd of the stage's re plane); M = 256 (pair), N = 128.
+template <int EB, int WHICH>
+__device__ __forceinline__ void stage_mmas(uint32_t d_re, uint32_t d_im, uint32_t a0, uint64_t bd,
+                                           uint32_t acc_first) {
+  constexpr uint32_t id_pos = (1u << 4) | ((128u >> 3) << 17) | ((256u >> 4) << 24);
+  constexpr uint32_t id_neg = id_pos | (1u << 14);
+  constexpr uint32_t kPlaneDesc = kPlane >> 4;   // descriptor address units
+  if constexpr (EB == 1) {
+    // per step: A columns re 8 | im 8, B K bytes 32
+#pragma unroll
+    for (int sub = 0; sub < Geo<EB>::kSteps; ++sub) {
+      const uint32_t a_re = a0 + 16 * sub, a_im = a_re + 8;
+      const uint64_t b_re = bd + 2 * sub, b_im = bd + kPlaneDesc + 2 * sub;
+      const uint32_t acc0 = sub > 0 ? 1u : acc_first;
+      if constexpr ((WHICH & 1) != 0) {
+        mma2_f8_tmem_a(d_re, a_re, b_re, id_pos, acc0);
+        mma2_f8_tmem_a(d_re, a_im, b_im, id_pos, 1u);
+      }
+      if constexpr ((WHICH & 2) != 0) {
+        mma2_f8_tmem_a(d_im, a_im, b_re, id_pos, acc0);
+        mma2_f8_tmem_a(d_im, a_re, b_im, id_neg, 1u);
+      }
+    }
+  } else {
+    // per step: A columns re 16 | im 16 (two K = 16 halves of 8 each),
+    // B K bytes 64 (two halves of 32)
+#pragma unroll
+    for (int sub = 0; sub < Geo<EB>::kSteps; ++sub)
+#pragma unroll
+      for (int kk = 0; kk < 2; ++kk) {
+        const uint32_t a_re = a0 + 32 * sub + 8 * kk, a_im = a_re + 16;
+        const uint64_t b_re = bd + 4 * sub + 2 * kk, b_im = bd + kPlaneDesc + 4 * sub + 2 * kk;
+        const uint32_t acc0 = (sub + kk) > 0 ? 1u : acc_first;
+        if constexpr ((WHICH & 1) != 0) {
+          mma2_f16_tmem_a(d_re, a_re, b_re, id_pos, acc0);
+          mma2_f16_tmem_a(d_re, a_im, b_im, id_pos, 1u);
+        }
+        if constexpr ((WHICH & 2) != 0) {
+          mma2_f16_tmem_a(d_im, a_im, b_re, id_pos, acc0);
+          mma2_f16_tmem_a(d_im, a_re, b_im, id_neg, 1u);
+        }
+      }
+  }
 }
 
 // Bias removal of one staged value: D holds sums of products of u * 2^-9
@@ -560,7 +622,8 @@ xcorr_tc8_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant
       mbar_init(&s.op_empty[k], 1);
     }
     mbar_init(s.acc_full, 1);
-    mbar_init(s.acc_empty, 8);       // both CTAs' epilogue warps (used in CTA 0)
+    mbar_init(s.acc_empty, 8);       // both CTAs' epilogue warps (used in CTA 0): D_re read
+    mbar_init(s.acc_empty_im, 8);    // the same for D_im
     for (int k = 0; k < 2; ++k) {
       mbar_init(&s.sums_full[k], kAWarps + 2 * kBWarps);  // own A and B warps, partner's B warps
       mbar_init(&s.sums_empty[k], 8);                     // own and partner's epilogue warps
@@ -652,57 +715,65 @@ xcorr_tc8_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant
       int ui = 0, st = 0;
       uint32_t ph = 0;                            // phase of operand slot st
       bool ok = true;
-      // A from tensor memory, B K-major; e4m3 x e4m3 or f16 x f16 -> f32, M = 256 (pair), N = 128
-      constexpr uint32_t id_pos = (1u << 4) | ((128u >> 3) << 17) | ((256u >> 4) << 24);
-      constexpr uint32_t id_neg = id_pos | (1u << 14);
-      constexpr uint32_t kSlotDesc = kOpStage >> 4, kPlaneDesc = kPlane >> 4;   // descriptor address units
+      constexpr uint32_t kSlotDesc = kOpStage >> 4;   // descriptor address units
       const uint64_t desc0 = sdesc_k_sw128(smem_u32(s.op));
       const uint32_t d_re = tmem, d_im = tmem + 128;
       for (int it = 0; it < s.sched[0] && ok; ++it, ++ui) {
         const Item w = item_at(s.sched, it);
-        if (!wait_or_abort(s.acc_empty, (ui & 1) ^ 1, lim, abort_flag)) {
+        const uint32_t free_par = (ui & 1) ^ 1;
+        // D is released in two halves.  Once the epilogue has read D_re, the
+        // real-part MMAs of the operand stages already resident (up to the
+        // whole ring) are issued while it still reads D_im; their imaginary
+        // parts follow the second release.
+        const int nst = (w.k1 - w.k0 + G::kSteps - 1) / G::kSteps;
+        const int head = nst < kOpStages ? nst : kOpStages;
+        if (!wait_or_abort(s.acc_empty, free_par, lim, abort_flag)) {
           fail(s, prm.err, kErrWaitAccEmpty);
           break;
         }
         tc_fence_after();
-        for (int ks = w.k0; ks < w.k1; ks += G::kSteps) {
+        {
+          int sh = st;
+          uint32_t phh = ph;
+          for (int p = 0; p < head; ++p) {
+            if (!wait_or_abort(&s.op_full[sh], phh, lim, abort_flag)) {
+              fail(s, prm.err, kErrWaitOpFull);
+              ok = false;
+              break;
+            }
+            tc_fence_after();
+            stage_mmas<EB, 1>(d_re, d_im, tmem + kTmemA0 + kTmemAStage * sh,
+                              desc0 + static_cast<uint64_t>(kSlotDesc * sh), p == 0 ? 0u : 1u);
+            if (++sh == kOpStages) {
+              sh = 0;
+              phh ^= 1u;
+            }
+          }
+        }
+        if (!ok) break;
+        if (!wait_or_abort(s.acc_empty_im, free_par, lim, abort_flag)) {
+          fail(s, prm.err, kErrWaitAccEmpty);
+          break;
+        }
+        tc_fence_after();
+        for (int p = 0; p < head; ++p) {
+          stage_mmas<EB, 2>(d_re, d_im, tmem + kTmemA0 + kTmemAStage * st,
+                            desc0 + static_cast<uint64_t>(kSlotDesc * st), p == 0 ? 0u : 1u);
+          commit2(&s.op_empty[st]);
+          if (++st == kOpStages) {
+            st = 0;
+            ph ^= 1u;
+          }
+        }
+        for (int ks = w.k0 + head * G::kSteps; ks < w.k1; ks += G::kSteps) {
           if (!wait_or_abort(&s.op_full[st], ph, lim, abort_flag)) {
             fail(s, prm.err, kErrWaitOpFull);
             ok = false;
             break;
           }
           tc_fence_after();
-          const uint32_t a0 = tmem + kTmemA0 + kTmemAStage * st;
-          const uint64_t bd = desc0 + static_cast<uint64_t>(kSlotDesc * st);
-          const uint32_t acc_first = ks == w.k0 ? 0u : 1u;   // the unit's (or part's) first stage overwrites D
-          if constexpr (EB == 1) {
-            // per step: A columns re 8 | im 8, B K bytes 32
-#pragma unroll
-            for (int sub = 0; sub < G::kSteps; ++sub) {
-              const uint32_t a_re = a0 + 16 * sub, a_im = a_re + 8;
-              const uint64_t b_re = bd + 2 * sub, b_im = bd + kPlaneDesc + 2 * sub;
-              const uint32_t acc0 = sub > 0 ? 1u : acc_first;
-              mma2_f8_tmem_a(d_re, a_re, b_re, id_pos, acc0);
-              mma2_f8_tmem_a(d_re, a_im, b_im, id_pos, 1u);
-              mma2_f8_tmem_a(d_im, a_im, b_re, id_pos, acc0);
-              mma2_f8_tmem_a(d_im, a_re, b_im, id_neg, 1u);
-            }
-          } else {
-            // per step: A columns re 16 | im 16 (two K = 16 halves of 8 each),
-            // B K bytes 64 (two halves of 32)
-#pragma unroll
-            for (int sub = 0; sub < G::kSteps; ++sub)
-#pragma unroll
-              for (int kk = 0; kk < 2; ++kk) {
-                const uint32_t a_re = a0 + 32 * sub + 8 * kk, a_im = a_re + 16;
-                const uint64_t b_re = bd + 4 * sub + 2 * kk, b_im = bd + kPlaneDesc + 4 * sub + 2 * kk;
-                const uint32_t acc0 = (sub + kk) > 0 ? 1u : acc_first;
-                mma2_f16_tmem_a(d_re, a_re, b_re, id_pos, acc0);
-                mma2_f16_tmem_a(d_re, a_im, b_im, id_pos, 1u);
-                mma2_f16_tmem_a(d_im, a_im, b_re, id_pos, acc0);
-                mma2_f16_tmem_a(d_im, a_re, b_im, id_neg, 1u);
-              }
-          }
+          stage_mmas<EB, 3>(d_re, d_im, tmem + kTmemA0 + kTmemAStage * st,
+                            desc0 + static_cast<uint64_t>(kSlotDesc * st), 1u);
           commit2(&s.op_empty[st]);
           if (++st == kOpStages) {
             st = 0;
@@ -901,7 +972,8 @@ xcorr_tc8_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant
     const int L = 32 * quad + lane;                 // TMEM lane = accumulator row; also a column index
     const int il = lane_to_input(L);                // input offset of row / column L in its tile
     const long long nbl = static_cast<long long>(prm.N) * (prm.N + 1) / 2;
-    int2* stg = s.stage + quad * kStageBufs * 32 * 32;
+    int* const sre = s.stage + quad * 2 * kStageBufs * kStageChunk;   // this warp's staged real parts
+    int* const sim = sre + kStageBufs * kStageChunk;                   // and imaginary parts
     bool ok = true;
     int ui = 0;
     for (int it = 0; it < s.sched[0]; ++it, ++ui) {
@@ -952,6 +1024,34 @@ xcorr_tc8_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant
       if (ok && t.write) {
         tc_fence_after();
         const uint32_t t_row = tmem + (static_cast<uint32_t>(32 * quad) << 16);
+        // D leaves tensor memory first, D_re and then D_im, each released as
+        // soon as it is read (the MMA starts the next unit's real parts in
+        // between): chunks 0-2 (32 columns each) as raw bits into shared
+        // staging, chunk 3 into registers (vb: re, va: im).  The bias removal
+        // and global writes run while the MMA works on the next unit.
+        uint32_t va[32], vb[32];
+        tmem_ld32(t_row, va);
+        tmem_ld32(t_row + 32, vb);
+        tmem_ld_wait();
+        stage_raw(sre, va, lane);
+        stage_raw(sre + kStageChunk, vb, lane);
+        tmem_ld32(t_row + 64, va);
+        tmem_ld32(t_row + 96, vb);
+        tmem_ld_wait();
+        stage_raw(sre + 2 * kStageChunk, va, lane);
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) arrive_relaxed_at(s.acc_empty, 0);
+#pragma unroll 1
+        for (int b = 0; b < 4; ++b) {
+          tmem_ld32(t_row + 128 + 32 * b, va);
+          tmem_ld_wait();
+          if (b < kStageBufs) stage_raw(sim + kStageChunk * b, va, lane);
+        }
+        tc_fence_before();
+        __syncwarp();
+        if (lane == 0) arrive_relaxed_at(s.acc_empty_im, 0);
+        released = true;
         // a part goes to its workspace slot (stored, never added): the tile's
         // first column input then lands on column 0
         const int accumulate = w.lo < 0 ? prm.accumulate : 0;
@@ -964,29 +1064,14 @@ xcorr_tc8_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant
         const bool tfull = t.transposed && t.tj * kTile + kTile <= prm.N;
         const int gI = t.ti * kTile + il;           // this lane's row input
         const int* ro = s.rowoff + 32 * quad;
-        // D leaves tensor memory first: chunks 0-2 (32 columns each) as raw
-        // bits into shared staging, chunk 3 into registers; then D is released
-        // and the bias removal and global writes run while the MMA works on the
-        // next unit.
-        uint32_t vre[32], vim[32];
-#pragma unroll 1
-        for (int cc = 0; cc < kTile; cc += 32) {
-          tmem_ld32(t_row + cc, vre);
-          tmem_ld32(t_row + 128 + cc, vim);
-          tmem_ld_wait();
-          if (cc < kStageBufs * 32) stage_raw(stg + (cc >> 5) * 1024, vre, vim, lane);
-        }
-        tc_fence_before();
-        __syncwarp();
-        if (lane == 0) arrive_relaxed_at(s.acc_empty, 0);
-        released = true;
 #pragma unroll 1
         for (int b = 0; b < 4; ++b) {
           const int cc = 32 * b;
-          const int2* sb = stg + (b == 3 ? 0 : b) * 1024;
+          const int* sb = sre + (b == 3 ? 0 : b) * kStageChunk;
           if (b == 3) {  // buffer 0 has been written out: chunk 3 goes there
             __syncwarp();
-            stage_raw(stg, vre, vim, lane);
+            stage_raw(sre, vb, lane);
+            stage_raw(sim, va, lane);
           }
           __syncwarp();
           if (!t.transposed) {
@@ -999,13 +1084,13 @@ xcorr_tc8_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant
 #pragma unroll 4
               for (int r = 0; r < 32; ++r) {
                 const float rre = __shfl_sync(0xFFFFFFFFu, row_re, r), rim = __shfl_sync(0xFFFFFFFFu, row_im, r);
-                accj[ro[r]] = unbias<EB>(sb[r * 32 + (lane ^ r)], rre, rim, cre, cim);
+                accj[ro[r]] = unbias<EB>(staged(sb, r, lane), rre, rim, cre, cim);
               }
             } else if (full) {
 #pragma unroll 4
               for (int r = 0; r < 32; ++r) {
                 const float rre = __shfl_sync(0xFFFFFFFFu, row_re, r), rim = __shfl_sync(0xFFFFFFFFu, row_im, r);
-                const int2 v = unbias<EB>(sb[r * 32 + (lane ^ r)], rre, rim, cre, cim);
+                const int2 v = unbias<EB>(staged(sb, r, lane), rre, rim, cre, cim);
                 int2* dst = accj + ro[r];
                 const int2 o = *dst;
                 *dst = make_int2(o.x + v.x, o.y + v.y);
@@ -1016,7 +1101,7 @@ xcorr_tc8_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant
                 const float rre = __shfl_sync(0xFFFFFFFFu, row_re, r), rim = __shfl_sync(0xFFFFFFFFu, row_im, r);
                 const int gi = t.ti * kTile + lane_to_input(32 * quad + r);
                 if (gi < prm.N && gj <= gi) {
-                  const int2 v = unbias<EB>(sb[r * 32 + (lane ^ r)], rre, rim, cre, cim);
+                  const int2 v = unbias<EB>(staged(sb, r, lane), rre, rim, cre, cim);
                   int2* dst = accj + ro[r];
                   if (accumulate) {
                     const int2 o = *dst;
@@ -1035,7 +1120,7 @@ xcorr_tc8_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant
 #pragma unroll 4
             for (int k = 0; k < 32; ++k) {
               if (tfull || t.tj * kTile + lane_to_input(cc + k) < prm.N) {
-                const int2 v = unbias<EB>(sb[lane * 32 + (k ^ lane)], row_re, row_im, s.colcorr[cc + k],
+                const int2 v = unbias<EB>(staged(sb, lane, k), row_re, row_im, s.colcorr[cc + k],
                                           s.colcorr[kTile + cc + k]);
                 int2* dst = acci + s.coloff[cc + k];
                 if (accumulate) {
@@ -1055,7 +1140,10 @@ xcorr_tc8_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant
         if (ok) tc_fence_after();
         tc_fence_before();
         __syncwarp();
-        if (lane == 0) arrive_relaxed_at(s.acc_empty, 0);
+        if (lane == 0) {
+          arrive_relaxed_at(s.acc_empty, 0);
+          arrive_relaxed_at(s.acc_empty_im, 0);
+        }
       }
       // all four warps are done with colcorr, rowoff, coloff and staging
       asm volatile("bar.sync 1, 128;" ::: "memory");
