@@ -65,6 +65,12 @@ SMALL_SHAPES = [  # (N, C, T): tile-ragged inputs, time tails, single samples
     (640, 1, 40),
     (736, 2, 33),
     (896, 1, 64),
+    # a unit's first stages are issued in two halves (real parts while the
+    # epilogue still reads D_im); stage counts at and just past the
+    # four-stage operand ring (e4m3 stages are 128 samples, f16 64)
+    (144, 3, 512),
+    (272, 2, 640),
+    (144, 2, 256),
 ]
 
 
