@@ -12,7 +12,9 @@ their float16 roundings (real and imaginary parts rounded separately); the
 oracle applies the same rounding (`round_weights`) and then evaluates the
 definition exactly in complex128.  Pinned in tests/test_beam_oracle.py by a
 hand-worked product, identity and linearity cases, a steered tone (closed
-form N * s_t) and an explicit loop.
+form N * s_t), an explicit loop, and binary16 roundings worked out by hand
+(ties, subnormals, overflow, parts rounding in different directions:
+tests/golden/beam_weight_rounding.txt).
 
 Arrays: x uint8 [T][C][N] (the X-engine's gulp layout, decoded by this
 module's own nibble decoder), w complex [C][B][N]; y complex128 [T][C][B].

@@ -62,3 +62,62 @@ def test_explicit_loop_matches_einsum_and_rounding_is_float16():
     wr = beam.round_weights(w)
     assert np.all(wr.real == w.real.astype(np.float16).astype(np.float64))
     assert np.abs(wr - w).max() <= 2.0 ** -11 * np.abs(w).max() * 2
+
+
+def _rounding_cases():
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "beam_weight_rounding.txt")
+    rows = []
+    with open(path) as f:
+        for line in f:
+            body = line.split("#", 1)[0].split()
+            if body:
+                rows.append([float(v) for v in body])
+    a = np.array(rows)
+    return a[:, 0] + 1j * a[:, 1], a[:, 2], a[:, 3]
+
+
+def _rtz16(x):
+    """Binary16 with truncation toward zero (a wrong reading, for the teeth check)."""
+    with np.errstate(over="ignore"):
+        r = x.astype(np.float16).astype(np.float64)
+    over = np.abs(r) > np.abs(x)
+    r[over] = np.nextafter(r[over].astype(np.float16), np.float16(0)).astype(np.float64)
+    return r
+
+
+def _bf16(x):
+    """bfloat16, round to nearest even (a wrong reading, for the teeth check)."""
+    b = np.asarray(x, np.float32).view(np.uint32).astype(np.uint64)
+    b = (b + 0x7FFF + ((b >> 16) & 1)) & 0xFFFF0000
+    return b.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def test_weight_rounding_matches_hand_derived_float16():
+    # tests/golden/beam_weight_rounding.txt: parts rounded separately to
+    # binary16, nearest with ties to even, overflow to infinity
+    w, re, im = _rounding_cases()
+    with np.errstate(over="ignore"):
+        got = beam.round_weights(w)
+    np.testing.assert_array_equal(got.real, re)
+    np.testing.assert_array_equal(got.imag, im)
+
+
+def test_weight_rounding_pins_reject_other_readings():
+    # each plausible misreading disagrees with at least one hand-derived row
+    w, re, im = _rounding_cases()
+    want = re + 1j * im
+    fin = np.isfinite(re)
+
+    def differs(r):
+        return bool(np.any(r[fin] != want[fin]))
+
+    assert differs(_rtz16(w.real) + 1j * _rtz16(w.imag))            # toward zero
+    assert differs(_bf16(w.real) + 1j * _bf16(w.imag))              # bfloat16
+    mag = np.abs(w)
+    with np.errstate(over="ignore", invalid="ignore"):
+        m16 = mag.astype(np.float16).astype(np.float64)
+        by_mag = np.where(mag > 0, w * (m16 / np.where(mag > 0, mag, 1)), 0)
+    assert differs(by_mag)                                           # magnitude rounded, angle kept
+    with np.errstate(over="ignore"):
+        assert differs(w.real.astype(np.float32).astype(np.float64) + 1j * w.imag)  # float32 only
