@@ -83,6 +83,32 @@ def measured_peaks() -> dict:
     return {"bf16": 1800.0, "bf16_sustained": 1400.0, "hbm": 6400.0, "source": "fallback"}
 
 
+def scaled_mm_fp8_tflops(dev, n: int = 8192, reps: int = 10):
+    """Dense e4m3 rate of the vendor GEMM on this GPU (torch._scaled_mm, n^3,
+    best of `reps`, CUDA events): a second denominator printed beside the
+    2 x bf16 one, so that neither flatters the kernel.  None if unsupported."""
+    import torch
+    try:
+        a = torch.randn(n, n, device=dev).to(torch.float8_e4m3fn)
+        b = torch.randn(n, n, device=dev).to(torch.float8_e4m3fn).t()
+        one = torch.ones((), device=dev)
+        for _ in range(3):
+            torch._scaled_mm(a, b, one, one, out_dtype=torch.bfloat16)
+        best = None
+        for _ in range(reps):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            torch._scaled_mm(a, b, one, one, out_dtype=torch.bfloat16)
+            e1.record()
+            e1.synchronize()
+            t = e0.elapsed_time(e1)
+            best = t if best is None else min(best, t)
+        del a, b
+        return 2.0 * n ** 3 / (best * 1e-3) / 1e12
+    except Exception:
+        return None
+
+
 def recorded_traffic(kernel_key: str):
     """Per-launch DRAM bytes from the committed ncu summary, if it was taken on
     the current kernel source; otherwise None."""
@@ -97,8 +123,16 @@ def recorded_traffic(kernel_key: str):
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled every 50 ms."""
+    """SM clock, power and throttle reasons sampled DURING the timed region.
 
+    NVML (nvidia-ml-py) is read from a thread every 2 ms, with one sample
+    taken synchronously as the region opens and one as it closes, so even a
+    region of a few milliseconds has at least two samples.  Without NVML the
+    sampler falls back to `nvidia-smi -lms 50` (read-only queries either way).
+    """
+
+    REASONS = (("hw_slowdown", 0x8), ("hw_thermal_slowdown", 0x40),
+               ("sw_thermal_slowdown", 0x20), ("sw_power_cap", 0x4))
     FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
               "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
               "clocks_event_reasons.sw_power_cap")
@@ -106,9 +140,51 @@ class ClockSampler:
     def __init__(self, index: int):
         self.index = index
         self.proc = None
+        self.nvml = None
+        self.handle = None
+        self.samples = []          # (sm_mhz, max_mhz, reason bit mask)
         self.lines = []
+        self.stop = threading.Event()
+        self.thread = None
+
+    def _handle(self):
+        import pynvml
+        pynvml.nvmlInit()
+        self.nvml = pynvml
+        try:   # the CUDA device's PCI address: NVML numbers every GPU of the host
+            import torch
+            p = torch.cuda.get_device_properties(self.index)
+            bus = f"{p.pci_domain_id:08X}:{p.pci_bus_id:02X}:{p.pci_device_id:02X}.0"
+            return pynvml.nvmlDeviceGetHandleByPciBusId(bus.encode())
+        except Exception:
+            return pynvml.nvmlDeviceGetHandleByIndex(self.index)
+
+    def sample(self):
+        n, h = self.nvml, self.handle
+        try:
+            sm = n.nvmlDeviceGetClockInfo(h, n.NVML_CLOCK_SM)
+            mx = n.nvmlDeviceGetMaxClockInfo(h, n.NVML_CLOCK_SM)
+            try:
+                r = n.nvmlDeviceGetCurrentClocksEventReasons(h)
+            except Exception:
+                r = n.nvmlDeviceGetCurrentClocksThrottleReasons(h)
+            self.samples.append((float(sm), float(mx), int(r)))
+        except Exception:
+            pass
+
+    def _poll(self):
+        while not self.stop.wait(0.002):
+            self.sample()
 
     def __enter__(self):
+        try:
+            self.handle = self._handle()
+            self.sample()                       # as the region opens
+            self.thread = threading.Thread(target=self._poll, daemon=True)
+            self.thread.start()
+            return self
+        except Exception:
+            self.handle = None
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
@@ -125,6 +201,11 @@ class ClockSampler:
             self.lines.append(line.strip())
 
     def __exit__(self, *exc):
+        if self.handle is not None:
+            self.sample()                       # as the region closes
+            self.stop.set()
+            self.thread.join(timeout=1)
+            return
         if self.proc:
             self.proc.terminate()
             try:
@@ -134,7 +215,12 @@ class ClockSampler:
 
     def summary(self) -> dict:
         sm, mx, reasons = [], 0.0, set()
-        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for c, m, r in self.samples:
+            sm.append(c)
+            mx = max(mx, m)
+            for name, bit in self.REASONS:
+                if r & bit:
+                    reasons.add(name)
         for l in self.lines:
             parts = [p.strip() for p in l.split(",")]
             if len(parts) < 7:
@@ -144,11 +230,12 @@ class ClockSampler:
                 mx = max(mx, float(parts[1]))
             except ValueError:
                 continue
-            for n, v in zip(names, parts[3:7]):
+            for (n, _), v in zip(self.REASONS, parts[3:7]):
                 if v.lower() == "active":
                     reasons.add(n)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx or None,
-                "reasons": sorted(reasons), "samples": len(sm)}
+                "reasons": sorted(reasons), "samples": len(sm),
+                "source": "nvml" if self.samples else "nvidia-smi"}
 
 
 def dist_setup():
@@ -419,16 +506,36 @@ def run_calib(args, world, rank, local, pg, dev):
         from oracle import calib as ocal
         nch = 32
         t0 = time.perf_counter()
-        ocal.chisq(g[:nch], m[:nch], v[:nch], w[:nch])
-        ocal.grad(g[:nch], m[:nch], v[:nch], w[:nch])
+        chi_ref = ocal.chisq(g[:nch], m[:nch], v[:nch], w[:nch])
+        grad_ref = ocal.grad(g[:nch], m[:nch], v[:nch], w[:nch])
         dt = time.perf_counter() - t0
+        # the GPU on the same sample (outside every timed region), against the
+        # oracle just timed and against central float64 finite differences
+        # (step 1e-6) of chi^2 at 32 sampled entries
+        sub = calib.Calibrator(N, nch)
+        chi_s, grad_s = sub.chisq_grad(dg[:nch], dm[:nch], dv[:nch], dw[:nch], True, stream=stream)
+        torch.cuda.synchronize(dev)
+        chi_s, grad_s = chi_s.item(), grad_s.cpu().numpy().astype(np.complex128)
+        sub.close()
+        gerr = np.abs(grad_s - grad_ref)
+        rng = np.random.default_rng(0)
+        ents = list(zip(rng.integers(0, nch, 32).tolist(), rng.integers(0, N, 32).tolist()))
+        fd = np.array([ocal.finite_difference_entry(g, m, v, w, True, c, k) for c, k in ents])
+        fd_err = np.abs(np.array([grad_s[c, k] for c, k in ents]) - fd)
         cpu = {"value": nch * nbl / dt / 1e9, "unit": "G baselines/s", "cores": 1, "kind": "oracle",
-               "sample": f"{nch} of {C} channels, all {nbl} baselines, chi^2 + gradient ({dt:.1f} s)"}
+               "sample": f"{nch} of {C} channels, all {nbl} baselines, chi^2 + gradient ({dt:.1f} s)",
+               "gpu_vs_oracle_on_sample": {
+                   "chisq_rel_err": abs(chi_s - chi_ref) / abs(chi_ref),
+                   "grad_max_abs_err_over_max_abs": float(gerr.max() / np.abs(grad_ref).max()),
+                   "grad_normwise_rel_err": float(np.linalg.norm(gerr) / np.linalg.norm(grad_ref)),
+                   "fd_entries": len(ents),
+                   "grad_vs_fd_max_rel_err": float((fd_err / np.abs(fd)).max()),
+                   "grad_vs_fd_normwise_rel_err": float(np.linalg.norm(fd_err) / np.linalg.norm(fd))}}
     if rank == 0:
         line = {
             "metric": CALIB_METRIC, "value": value, "unit": "G baselines/s", "n_gpus": world,
             "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": ms,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32 (chi^2 sum f64)",
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32 (chi^2: compensated f32 per warp, f64 across warps)",
             "data": "synthetic (seeded gains, 5-source sky model, noisy V_obs)",
             "config": {"workload": WORKLOADS["calib"][1], "n_input": N, "n_chan": C, "weights": "ones (read)",
                        "l2": f"inputs ({(m.nbytes + v.nbytes + w.nbytes) >> 20} MiB) exceed L2 (126 MB); no flush",
@@ -789,9 +896,28 @@ def run_ours(args):
         torch.cuda.synchronize(dev)
         e32.check()
         ms32 = a.elapsed_time(b) / n32
+        # its ceiling: one dp4a per useful complex MAC (two per time-sample
+        # pair, Re and Im), against the measured dp4a issue rate x SMs x the
+        # SM clock sampled while it ran
+        with ClockSampler(local) as clk32:
+            a.record(stream)
+            e32.correlate_emit(gulp, vis, stream=stream)
+            b.record(stream)
+            torch.cuda.synchronize(dev)
+        mhz = clk32.summary()["sm_mhz"] or 0.0
+        rate = xe.dp4a_rate_per_sm_clock(dev)
+        sms = torch.cuda.get_device_properties(dev).multi_processor_count
+        peak_dp4a = rate * sms * mhz * 1e6 if mhz else None
+        achieved_dp4a = step_cmac / (ms32 * 1e-3)
         int32_line = {"value": step_cmac / (ms32 * 1e-3) / 1e12, "unit": "cMAC TOPS",
                       "ms_per_step": ms32, "speedup_of_tensor_path": (step_cmac / (ms * 1e-3) / 1e12) /
-                      (step_cmac / (ms32 * 1e-3) / 1e12)}
+                      (step_cmac / (ms32 * 1e-3) / 1e12),
+                      "roofline": {"bound": "alu", "unit": "dp4a/s", "achieved": achieved_dp4a,
+                                   "peak": peak_dp4a,
+                                   "frac": (achieved_dp4a / peak_dp4a) if peak_dp4a else None,
+                                   "dp4a_per_sm_clock": rate, "sm_mhz": mhz,
+                                   "peak_source": "measured dp4a issue rate (xe_probe_dp4a_rate) x SMs "
+                                                  "x SM clock sampled during the int32 launch"}}
         e32.close()
 
     # ---- end to end through the host-buffer C-ABI call
@@ -863,8 +989,11 @@ def run_ours(args):
         peak = None
         peak_note = "CUDA-core path: no tensor peak"
         key = "xcorr_cudacore"
+    mm8 = scaled_mm_fp8_tflops(dev) if args.operand == "fp8" else None
     roofline = {"bound": "tensor" if peak else "alu", "achieved": achieved, "peak": peak,
                 "unit": "TFLOP/s", "frac": (achieved / peak) if peak else None,
+                "scaled_mm_fp8_tflops": mm8,
+                "frac_of_scaled_mm_fp8": (achieved / mm8) if mm8 else None,
                 "traffic": recorded_traffic(key), "kernel": key, "kernel_ms": kern_ms,
                 "kernel_ms_per_step": kern_stats,
                 "peak_source": peak_note,

@@ -198,15 +198,30 @@ XE_API xe_status xe_correlate_host(xe_plan_t plan, const uint8_t *h_gulp, int nt
  *    ntime = 0 writes zeros.  Same alignment rules as the plan calls.
  *  - The first call on a device looks up the scratch's device address
  *    (cudaGetSymbolAddress) with that device current; make that first call
- *    before any stream capture.
- *  - Every call shares the scratch and clears what must start at zero (the
- *    error word); calls whose GPU work overlaps, e.g. on different streams,
- *    race on it and must be serialised by the caller.
- *  - Asynchronous on `stream`; errors as for the plan calls.
+ *    before any stream capture.  The address is kept for the life of the
+ *    process: do not use these calls across a cudaDeviceReset.
+ *  - Every call shares the scratch and overwrites the integration buffer
+ *    before adding to it; calls whose GPU work overlaps, e.g. on different
+ *    streams, race on it and must be serialised by the caller.
+ *  - Asynchronous on `stream`.  Argument errors and launch failures are
+ *    returned at once, as for the plan calls.  A device wait that times out
+ *    (XE_ERR_TIMEOUT for a plan, through xe_plan_check) is recorded in the
+ *    scratch's error word, which only xe_correlate_noalloc_check reads:
+ *    call it once the stream has drained the work, before trusting d_vis.
  */
 XE_API xe_status xe_correlate_noalloc(const uint8_t *d_gulp, int ntime, int n_chan,
                                       int n_input, xe_out out_type, void *d_vis,
                                       void *stream);
+
+/*
+ * Outcome of the allocation-free calls so far: synchronises `stream`, reads
+ * the scratch's error word and clears it.  XE_OK if no device wait of any
+ * xe_correlate_noalloc call since the previous check timed out, else
+ * XE_ERR_TIMEOUT (the visibilities of those calls are not to be trusted);
+ * XE_ERR_CUDA if the synchronisation or the copy fails.  Allocates nothing.
+ * (No counterpart in the paper.)
+ */
+XE_API xe_status xe_correlate_noalloc_check(void *stream);
 
 /* ------------------------------------------------------------------------
  * Gain calibration on emitted visibilities (weighted chi^2 and its adjoint).
@@ -220,7 +235,8 @@ XE_API xe_status xe_correlate_noalloc(const uint8_t *d_gulp, int ntime, int n_ch
  * [n_chan][n_input]; d_model (C_ij) and d_vobs (V_ij) [n_chan][n_input *
  * (n_input + 1) / 2] in the visibility layout above; d_w float32 weights in
  * the same layout, or NULL for all ones.  Complex pointers must be 8-byte
- * aligned.  Per-baseline terms are float32; chi^2 is summed in float64; both
+ * aligned.  Per-baseline terms are float32; chi^2 is summed in float32 with a
+ * compensation term per thread and warp, and the per-warp sums in float64; both
  * results are deterministic.  The object owns its scratch (per-CTA chi^2
  * partials and the adjoint's partial sums); calls on one object must not
  * overlap.  Errors: XE_ERR_INVALID_ARG for a NULL handle or required pointer
@@ -403,6 +419,21 @@ XE_API const char *xe_plan_last_error(xe_plan_t plan);
 
 /* Library version string. */
 XE_API const char *xe_version(void);
+
+/* ------------------------------------------------------------------------
+ * Measurement aid (no counterpart in the paper): the CUDA cores' dp4a issue
+ * rate, the arithmetic ceiling of the plain int32 X-engine
+ * (XE_OPERAND_INT32_CUDACORE), which spends one dp4a per complex
+ * multiply-accumulate.  Launches `ctas` CTAs of 256 threads; every thread
+ * issues iters * 256 dp4a in 8 independent chains on register operands.
+ * d_cycles[ctas] (int64) receives each CTA's clock64 cycles, d_sink[ctas *
+ * 256] (int32) the threads' sums; *dp4a_per_cta is set on the host.  Rate
+ * per SM and clock = dp4a_per_cta * (CTAs per SM) / cycles.  Asynchronous on
+ * `stream`; XE_ERR_INVALID_ARG for iters outside 1..2^20, ctas outside
+ * 1..2^16 or a NULL pointer.
+ * ---------------------------------------------------------------------- */
+XE_API xe_status xe_probe_dp4a_rate(int iters, int ctas, long long *d_cycles, int *d_sink,
+                                    long long *dp4a_per_cta, void *stream);
 
 #ifdef __cplusplus
 }

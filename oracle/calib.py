@@ -117,3 +117,41 @@ def finite_difference_grad(g, model, vobs, w=None, include_autos=True, step=1e-6
                           chisq(gm, model, vobs, w, include_autos)) / (2 * step))
         out[(c, k)] = parts[0] + 1j * parts[1]
     return out
+
+
+def chisq_of_input(g, model, vobs, w, include_autos: bool, c: int, k: int) -> float:
+    """The part of chi2 that involves g[c][k]: the terms of baselines (k, j),
+    j <= k (row k, autocorrelation included) and (i, k), i > k (column k below
+    the diagonal), each counted once.  The rest of chi2 does not depend on
+    g[c][k], so central differences of this part in g[c][k] equal those of
+    chi2 itself, without the cancellation of a sum over every baseline."""
+    gc = np.asarray(g[c], dtype=np.complex128)
+    n = gc.shape[0]
+    j = np.arange(k + 1)
+    i = np.arange(k + 1, n)
+    p = np.concatenate([k * (k + 1) // 2 + j, i * (i + 1) // 2 + k])
+    gi = np.concatenate([np.full(k + 1, gc[k]), gc[i]])
+    gj = np.concatenate([gc[j], np.full(n - k - 1, gc[k])])
+    m = np.asarray(model[c], np.complex128)[p]
+    r = np.asarray(vobs[c], np.complex128)[p] - gi * np.conj(gj) * m
+    ww = np.ones(p.shape) if w is None else np.asarray(w[c], np.float64)[p]
+    if not include_autos:
+        ww = np.where(p == k * (k + 1) // 2 + k, 0.0, ww)
+    return float(np.sum(ww * (r.real ** 2 + r.imag ** 2)))
+
+
+def finite_difference_entry(g, model, vobs, w, include_autos: bool, c: int, k: int,
+                            step: float = 1e-6) -> complex:
+    """Central differences of chi2 in Re g[c][k] and Im g[c][k] (through
+    chisq_of_input): dRe + i dIm."""
+    g = np.array(g, dtype=np.complex128)
+    parts = []
+    for d in (step, 1j * step):
+        g0 = g[c, k]
+        g[c, k] = g0 + d
+        fp = chisq_of_input(g, model, vobs, w, include_autos, c, k)
+        g[c, k] = g0 - d
+        fm = chisq_of_input(g, model, vobs, w, include_autos, c, k)
+        g[c, k] = g0
+        parts.append((fp - fm) / (2 * step))
+    return parts[0] + 1j * parts[1]

@@ -9,10 +9,13 @@
 // One pass over the triangle (calib_pass_kernel) computes the partial sums of
 // chi^2, of the gradient, or of both: HBM-bound (each baseline's V and C, 8
 // bytes each, and w, 4 bytes, are read once).  A small second kernel
-// (calib_combine_kernel) adds the partials in a fixed order.  Per-baseline terms are float32.  chi^2 is summed per thread in
-// float32 over at most 2 x kGroup terms and from there on in float64; the
-// gradient is summed in float32.  Every summation order is fixed by the
-// problem size and the grid, so both results are deterministic.
+// (calib_combine_kernel) adds the partials in a fixed order.  Per-baseline
+// terms are float32.  chi^2 is summed in float32 with a compensation term
+// (TwoSum, Knuth) per thread and across the warp, so the pass kernel holds
+// no float64; only the final reduction of the per-warp (sum, compensation)
+// pairs in calib_combine_kernel is float64.  The gradient is summed in
+// float32.  Every summation order is fixed by the problem size and the grid,
+// so both results are deterministic.
 #include <cuda_runtime.h>
 
 #include <cstddef>
@@ -69,7 +72,7 @@ struct Geometry {
 };
 
 struct Scratch {
-  double* chi_part;    // [W]   chi^2 per warp
+  float2* chi_part;    // [W]   chi^2 per warp: float32 sum and its compensation
   float2* row_part;    // [C][S][N] row sums per (stripe, row)
   float2* col_part;    // [C T + W][64] column sums of warp w for tile gt (= c T + tile) at row w + gt
                        // (unique: a later warp never touches an earlier tile)
@@ -194,6 +197,24 @@ __device__ __forceinline__ float reduce4(float x0, float x1, float x2, float x3,
   return z;
 }
 
+// Compensated float32 sum (Knuth's TwoSum): after add(x), s + c equals the
+// exact sum of everything added, up to the rounding of c's own additions.
+struct CompSum {
+  float s = 0.f, c = 0.f;
+  __device__ __forceinline__ void add(float x) {
+    const float t = s + x;
+    const float z = t - s;
+    c += (s - (t - z)) + (x - z);
+    s = t;
+  }
+  // this lane's (s, c) plus the partner lane's at XOR distance o
+  __device__ __forceinline__ void add_lane(int o) {
+    const float ps = __shfl_xor_sync(0xFFFFFFFFu, s, o), pc = __shfl_xor_sync(0xFFFFFFFFu, c, o);
+    c += pc;
+    add(ps);
+  }
+};
+
 template <bool kChi, bool kGrad, bool kW>
 __global__ void __launch_bounds__(kThreads, kMinBlocks)
 calib_pass_kernel(const float2* __restrict__ g, const float2* __restrict__ model, const float2* __restrict__ vobs,
@@ -276,7 +297,7 @@ calib_pass_kernel(const float2* __restrict__ g, const float2* __restrict__ model
     gj1 = j1 < G.N ? gc[j1] : make_float2(0.f, 0.f);
   };
   if (n > 0) load_gj();
-  double chi_acc = 0.0;
+  CompSum chi_acc;
 
   const int groups = (n + kGroup - 1) / kGroup;
   for (int grp = 0; grp < groups; ++grp) {
@@ -333,7 +354,7 @@ calib_pass_kernel(const float2* __restrict__ g, const float2* __restrict__ model
       float t = chi_g[0];
 #pragma unroll
       for (int r = 1; r < kGroup; ++r) t += chi_g[r];
-      chi_acc += static_cast<double>(t);
+      chi_acc.add(t);
     }
     if (kGrad) {
       if constexpr (kGroup == 4) {
@@ -361,8 +382,8 @@ calib_pass_kernel(const float2* __restrict__ g, const float2* __restrict__ model
   }
   if (kChi) {
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) chi_acc += __shfl_xor_sync(0xFFFFFFFFu, chi_acc, o);
-    if (lane == 0) sc.chi_part[w] = chi_acc;
+    for (int o = 16; o > 0; o >>= 1) chi_acc.add_lane(o);
+    if (lane == 0) sc.chi_part[w] = make_float2(chi_acc.s, chi_acc.c);
   }
 
 }
@@ -436,7 +457,10 @@ calib_combine_kernel(Geometry G, Scratch sc, const double* __restrict__ scale, f
     for (int q0 = threadIdx.x; q0 < G.W; q0 += 8 * 256) {
       double p[8];
 #pragma unroll
-      for (int u = 0; u < 8; ++u) p[u] = q0 + u * 256 < G.W ? __ldcg(sc.chi_part + q0 + u * 256) : 0.0;
+      for (int u = 0; u < 8; ++u) {
+        const float2 e = q0 + u * 256 < G.W ? __ldcg(sc.chi_part + q0 + u * 256) : make_float2(0.f, 0.f);
+        p[u] = static_cast<double>(e.x) + static_cast<double>(e.y);
+      }
 #pragma unroll
       for (int u = 0; u < 8; ++u) acc += p[u];
     }
@@ -483,7 +507,7 @@ inline size_t align256(size_t x) { return (x + 255) & ~static_cast<size_t>(255);
 // partials) and the total.
 inline void layout(const Geometry& G, size_t off[4], size_t* total) {
   size_t o = 0;
-  off[0] = o; o = align256(o + sizeof(double) * G.W);
+  off[0] = o; o = align256(o + sizeof(float2) * G.W);
   off[1] = o; o = align256(o + sizeof(float2) * static_cast<size_t>(G.C) * G.S * G.N);
   off[2] = o; o = align256(o + sizeof(float2) * kStripe * (static_cast<size_t>(G.C) * G.T + G.W));
   off[3] = o; o = align256(o + sizeof(int2) * static_cast<size_t>(G.C) * G.T);
@@ -495,7 +519,7 @@ inline Scratch carve(void* base, const Geometry& G) {
   layout(G, off, &total);
   char* b = static_cast<char*>(base);
   Scratch sc;
-  sc.chi_part = reinterpret_cast<double*>(b + off[0]);
+  sc.chi_part = reinterpret_cast<float2*>(b + off[0]);
   sc.row_part = reinterpret_cast<float2*>(b + off[1]);
   sc.col_part = reinterpret_cast<float2*>(b + off[2]);
   sc.tile_w = reinterpret_cast<int2*>(b + off[3]);

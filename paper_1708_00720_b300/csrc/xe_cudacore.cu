@@ -199,11 +199,24 @@ __global__ void unpack_kernel(const uint8_t* __restrict__ in, int8_t* __restrict
   }
 }
 
+// SMs of the current device (grids of the element-wise kernels are capped
+// at a few waves of resident CTAs; grid-stride loops cover the rest).
+static long long current_sms() {
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) {
+    cudaGetLastError();
+    sms = 1;
+  }
+  return sms;
+}
+
 cudaError_t launch_unpack(const uint8_t* packed, int8_t* out, long long n, cudaStream_t stream) {
   if (n <= 0) return cudaSuccess;
   long long blocks = (n / 16 + 255) / 256;
   if (blocks < 1) blocks = 1;
-  if (blocks > 148 * 32) blocks = 148 * 32;
+  const long long cap = current_sms() * 32;   // 8 resident 256-thread CTAs per SM, 4 waves
+  if (blocks > cap) blocks = cap;
   unpack_kernel<<<static_cast<int>(blocks), 256, 0, stream>>>(packed, out, n);
   return cudaGetLastError();
 }
@@ -221,7 +234,8 @@ __global__ void emit_cf32_kernel(const int2* __restrict__ acc, float2* __restric
 cudaError_t launch_emit_cf32(const int32_t* acc, float* out, long long n_pairs, cudaStream_t stream) {
   if (n_pairs <= 0) return cudaSuccess;
   long long blocks = (n_pairs + 255) / 256;
-  if (blocks > 148 * 16) blocks = 148 * 16;
+  const long long cap = current_sms() * 16;
+  if (blocks > cap) blocks = cap;
   emit_cf32_kernel<<<static_cast<int>(blocks), 256, 0, stream>>>(
       reinterpret_cast<const int2*>(acc), reinterpret_cast<float2*>(out), n_pairs);
   return cudaGetLastError();

@@ -11,8 +11,11 @@
 //
 // The array is defined once in this library and every GPU that loads the
 // library keeps it until the process exits.  All calls share it: a call
-// clears what must start at zero, and calls whose GPU work overlaps (for
-// example on two streams) race on it.
+// overwrites the integration buffer before it adds to it, and calls whose GPU
+// work overlaps (for example on two streams) race on it.  The error word is
+// sticky: kernels OR their timeout codes into it and only
+// xe_correlate_noalloc_check reads and clears it, so a timeout of any call
+// since the last check is reported there.
 #include <cuda.h>
 #include <cuda_runtime.h>
 
@@ -50,7 +53,9 @@ std::mutex g_setup_mutex;
 void* g_scratch_addr[kMaxDevices] = {};
 
 // Device address of the scratch on the current device, looked up once per
-// device (with that device current) and cached.
+// device (with that device current) and cached.  The cache is not refreshed
+// after cudaDeviceReset, which unloads the module: the entry points must not
+// be used across a reset of the device.
 xe_status scratch_address(void** out) {
   int dev = 0;
   if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return XE_ERR_CUDA;
@@ -119,8 +124,8 @@ extern "C" XE_API xe_status xe_correlate_noalloc(const uint8_t* d_gulp, int ntim
   cudaStream_t s = static_cast<cudaStream_t>(stream);
   const size_t out_bytes = static_cast<size_t>(pairs) * 8;
 
-  // The error word keeps the previous call's value: clear it.
-  if (cudaMemsetAsync(d_err, 0, sizeof(int), s) != cudaSuccess) return XE_ERR_CUDA;
+  // The error word is not cleared here: it collects the timeouts of every
+  // call until xe_correlate_noalloc_check reads it.
   if (ntime == 0) return cudaMemsetAsync(d_vis, 0, out_bytes, s) == cudaSuccess ? XE_OK : XE_ERR_CUDA;
 
   EncodeTiledFn enc = encode_fn();
@@ -163,4 +168,19 @@ extern "C" XE_API xe_status xe_correlate_noalloc(const uint8_t* d_gulp, int ntim
                       ? cudaMemcpyAsync(d_vis, d_acc, out_bytes, cudaMemcpyDeviceToDevice, s)
                       : xe::launch_emit_cf32(d_acc, static_cast<float*>(d_vis), pairs, s);
   return e == cudaSuccess ? XE_OK : XE_ERR_CUDA;
+}
+
+extern "C" XE_API xe_status xe_correlate_noalloc_check(void* stream) {
+  void* scratch = nullptr;
+  xe_status st = scratch_address(&scratch);
+  if (st != XE_OK) return st;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  if (cudaStreamSynchronize(s) != cudaSuccess) return XE_ERR_CUDA;
+  int err = 0;
+  // a synchronous copy into this stack variable: the runtime stages it, this
+  // library allocates nothing
+  if (cudaMemcpy(&err, scratch, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return XE_ERR_CUDA;
+  if (err == 0) return XE_OK;
+  if (cudaMemset(scratch, 0, sizeof(int)) != cudaSuccess) return XE_ERR_CUDA;
+  return XE_ERR_TIMEOUT;
 }

@@ -134,6 +134,7 @@ struct StreamImpl {
 struct ServiceImpl {
   long long cap = 0, used = 0;
   int flags = 0;
+  int num_sms = 148;   // of the service's device; a dry run models a 148-SM B300
   bool dry = false, manual = false;
   std::mutex mu;
   std::condition_variable cv;
@@ -435,10 +436,20 @@ XE_API xe_status xe_service_create(xe_service_t* out, long long mem_cap_bytes, i
     }
     cap = static_cast<long long>(fr / 2);   // admission cap: half of the free HBM
   }
+  int sms = 148;
+  if (!dry) {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) {
+      cudaGetLastError();
+      return XE_ERR_CUDA;
+    }
+  }
   auto* svc = new (std::nothrow) xe_service();
   if (!svc) return XE_ERR_NOMEM;
   ServiceImpl& S = svc->impl;
   S.cap = cap;
+  S.num_sms = sms;
   S.flags = flags;
   S.dry = dry;
   S.manual = flags & XE_SERVICE_MANUAL;
@@ -481,9 +492,10 @@ XE_API xe_status xe_service_add_stream(xe_service_t svc, const xe_stream_config*
   const long long nbl = static_cast<long long>(c.n_input) * (c.n_input + 1) / 2;
   s->vis_bytes = static_cast<size_t>(c.n_chan) * nbl * 8;
   // device: ring + plan accumulator + visibility buffer + the plan's scratch
-  // for time-sliced units (as on a 148-SM B300) + 1 MiB of other plan memory
+  // for time-sliced units (sized by the device's SM count) + 1 MiB of other
+  // plan memory
   s->dev_bytes = static_cast<long long>(c.ring_gulps) * s->gulp_bytes + 2LL * s->vis_bytes +
-                 static_cast<long long>(xe::split_workspace_bytes(148)) + (1LL << 20);
+                 static_cast<long long>(xe::split_workspace_bytes(S.num_sms)) + (1LL << 20);
   s->host_bytes = static_cast<long long>(c.ring_gulps) * s->gulp_bytes + kOutSlots * static_cast<long long>(s->vis_bytes);
   std::lock_guard<std::mutex> lk(S.mu);
   if (S.used + s->dev_bytes > S.cap) {

@@ -78,6 +78,7 @@ def _load() -> ctypes.CDLL:
         "xe_status_string": ([I], ctypes.c_char_p),
         "xe_plan_last_error": ([P], ctypes.c_char_p),
         "xe_version": ([], ctypes.c_char_p),
+        "xe_probe_dp4a_rate": ([I, I, P, P, ctypes.POINTER(LL), P], I),
     }
     for name, (args, res) in sigs.items():
         fn = getattr(lib, name)
@@ -191,6 +192,24 @@ def xe_plan_launch_count(plan) -> int:
     out = ctypes.c_longlong()
     _check(_lib.xe_plan_launch_count(plan, ctypes.byref(out)), "xe_plan_launch_count")
     return out.value
+
+
+def dp4a_rate_per_sm_clock(device=None, iters: int = 4096) -> float:
+    """Measured dp4a issue rate of the CUDA cores: dp4a per SM per clock
+    (the arithmetic ceiling of the plain int32 X-engine)."""
+    import torch
+    dev = torch.device("cuda", torch.cuda.current_device()) if device is None else device
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    ctas = 4 * sms                      # 4 x 256 threads = 32 warps per SM
+    cycles = torch.zeros(ctas, dtype=torch.int64, device=dev)
+    sink = torch.zeros(ctas * 256, dtype=torch.int32, device=dev)
+    per = ctypes.c_longlong()
+    for _ in range(2):                   # the first launch warms up
+        _check(_lib.xe_probe_dp4a_rate(iters, ctas, cycles.data_ptr(), sink.data_ptr(),
+                                       ctypes.byref(per), _stream(None)), "xe_probe_dp4a_rate")
+    torch.cuda.synchronize(dev)
+    # 4 co-resident CTAs share an SM: its rate is 4 CTAs' dp4a over their span
+    return 4.0 * per.value / float(cycles.double().median())
 
 
 def status_of(fn, *args) -> int:

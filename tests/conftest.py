@@ -11,6 +11,8 @@ if ROOT not in sys.path:
 def pytest_configure(config):
     config.addinivalue_line(
         "markers", "gpu: needs a CUDA device (B300, sm_103a) and the built library")
+    config.addinivalue_line(
+        "markers", "fullsize: full-size workloads checked over every baseline (minutes of oracle time)")
 
 
 @pytest.fixture(scope="session")

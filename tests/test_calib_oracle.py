@@ -130,3 +130,38 @@ def test_autos_only_single_input():
     g, m, v, w, chi, gr = read_hand()
     assert calib.chisq(g, m, v, w, include_autos=False) == 0.0
     assert calib.grad(g, m, v, w, include_autos=False)[0, 0] == 0.0
+
+
+@pytest.mark.parametrize("include_autos", [True, False])
+def test_input_part_of_chisq_carries_every_change(include_autos):
+    # chi2 minus chisq_of_input(c, k) must not depend on g[c][k]: perturb it
+    # and compare the two changes, and compare the derived central
+    # differences with those of the whole chi2
+    g, m, v, w = random_problem(C=2, N=9, seed=5)
+    for (c, k) in [(0, 0), (1, 4), (0, 8), (1, 8)]:
+        gp = g.copy()
+        gp[c, k] += 0.37 - 0.21j
+        full = calib.chisq(gp, m, v, w, include_autos) - calib.chisq(g, m, v, w, include_autos)
+        part = (calib.chisq_of_input(gp, m, v, w, include_autos, c, k) -
+                calib.chisq_of_input(g, m, v, w, include_autos, c, k))
+        assert part == pytest.approx(full, rel=1e-12, abs=1e-12)
+        fd_full = calib.finite_difference_grad(g, m, v, w, include_autos, index=[(c, k)])[(c, k)]
+        fd_part = calib.finite_difference_entry(g, m, v, w, include_autos, c, k)
+        assert abs(fd_part - fd_full) <= 1e-6 * abs(fd_full)
+        assert abs(fd_part - calib.grad(g, m, v, w, include_autos)[c, k]) <= 1e-6 * abs(fd_full)
+
+
+def test_input_part_rejects_a_dropped_column():
+    # counting only row k (a plausible slip) misses terms that change with g_k
+    g, m, v, w = random_problem(C=1, N=6, seed=6)
+    c, k = 0, 2
+    gp = g.copy()
+    gp[c, k] += 0.5
+    full = calib.chisq(gp, m, v, w) - calib.chisq(g, m, v, w)
+    n = g.shape[1]
+    ii, jj = np.tril_indices(n)
+    row = ii == k
+    r0 = calib.residuals(g, m, v)[0, row]
+    r1 = calib.residuals(gp, m, v)[0, row]
+    only_row = float(np.sum(w[0, row] * (np.abs(r1) ** 2 - np.abs(r0) ** 2)))
+    assert abs(only_row - full) > 1e-6 * abs(full)

@@ -237,9 +237,11 @@ def test_argument_errors(cal):
     assert st == xe.XE_ERR_INVALID_ARG
 
 
-def test_calibration_workload_full_size(cal):
+@pytest.fixture(scope="module")
+def calib_workload(cal):
     """512 inputs, 128 channels: V_obs from the oracle X-engine on the seeded
-    voltages (64 samples, to keep the oracle fast), a sky model and random gains."""
+    voltages (64 samples, to keep the oracle fast), a sky model and random
+    gains; the GPU's chi^2 and gradient of it."""
     import torch
     p = synth.CALIB_CONFIG
     N, C = p["n_input"], p["n_chan"]
@@ -253,8 +255,53 @@ def test_calibration_workload_full_size(cal):
     k = cal.Calibrator(N, C)
     chi, grad = k.chisq_grad(dg, dm, dv, dw, True)
     torch.cuda.synchronize()
-    check_chisq(chi.item(), g, m, vobs, w, True)
-    check_grad(grad.cpu().numpy(), g, m, vobs, w, True)
+    out = (g, m, vobs, w, chi.item(), grad.cpu().numpy())
+    k.close()
+    return out
+
+
+def test_calibration_workload_full_size(calib_workload):
+    g, m, vobs, w, chi, grad = calib_workload
+    ref = check_chisq(chi, g, m, vobs, w, True)
+    check_grad(grad, g, m, vobs, w, True)
+    want = ocal.grad(g, m, vobs, w, True)
+    err = np.abs(grad.astype(np.complex128) - want)
+    print(f"\ncalibration 512x128 vs the float64 oracle: chi^2 rel {abs(chi - ref) / ref:.3e}; "
+          f"gradient max |err| / max |grad| {err.max() / np.abs(want).max():.3e}, "
+          f"normwise {np.linalg.norm(err) / np.linalg.norm(want):.3e}")
+
+
+def test_calibration_workload_gradient_vs_finite_differences(calib_workload):
+    """The GPU gradient at 96 sampled (channel, input) entries against central
+    float64 finite differences (step 1e-6) of the float64 chi^2 in Re g and
+    Im g.  Only the baselines of input k change with g_k, so the differences
+    are taken of that part of chi^2 (oracle.calib.chisq_of_input), free of the
+    cancellation of the whole sum; chi^2 is quadratic in g_k except for the
+    autocorrelation term, so the truncation error is negligible."""
+    g, m, vobs, w, chi, grad = calib_workload
+    C, N = g.shape
+    rng = np.random.default_rng(11)
+    idx = [(int(c), int(k)) for c, k in zip(rng.integers(0, C, 90), rng.integers(0, N, 90))]
+    idx += [(0, 0), (0, N - 1), (C - 1, 0), (C - 1, N - 1), (5, 63), (5, 64)]
+    tol = grad_tol(g, m, vobs, w, True)
+    step = 1e-6
+    fd = np.array([ocal.finite_difference_entry(g, m, vobs, w, True, c, k, step) for c, k in idx])
+    got = np.array([grad[c, k] for c, k in idx]).astype(np.complex128)
+    an = np.array([ocal.grad_entry(g, m, vobs, w, True, c, k) for c, k in idx])
+    # rounding of a central difference: each of its float64 chi^2 parts errs
+    # by at most ~16 * 2^-53 of itself (pairwise sums), divided by 2 step,
+    # for the real and the imaginary direction
+    part = np.array([ocal.chisq_of_input(g, m, vobs, w, True, c, k) for c, k in idx])
+    fd_err = 2 * 16 * 2.0 ** -53 * part / (2 * step) * np.sqrt(2)
+    assert np.all(np.abs(fd - an) <= fd_err + 1e-9 * np.abs(an))
+    err = np.abs(got - fd)
+    bound = np.array([tol[c, k] for c, k in idx]) + fd_err
+    assert np.all(err <= bound), np.argwhere(err > bound)[:5]
+    rel = err / np.abs(fd)
+    normwise = np.linalg.norm(err) / np.linalg.norm(fd)
+    assert rel.max() <= 1e-5 and normwise <= 1e-5, (rel.max(), normwise)
+    print(f"\ncalibration 512x128, {len(idx)} entries vs float64 central differences: "
+          f"max rel {rel.max():.3e}, normwise {normwise:.3e}")
 
 
 def test_maximum_inputs_sampled(cal):

@@ -144,3 +144,33 @@ def test_bounded_device_wait_reports_timeout_and_context_survives(sv):
     torch.cuda.synchronize()
     np.testing.assert_array_equal(v.cpu().numpy(), oracle.correlate(x))
     eng.close()
+
+
+def test_serving_workload_shapes_bit_exact(sv):
+    """The serving workload's three streams (256 inputs x 64 channels, 512 x
+    128, 1024 x 256; gulps of 1024 samples, rings of 8, integrations of 8
+    gulps) through the service at once.  Each stream's first integration is
+    compared with the oracle on every baseline: all channels of the 256-input
+    stream, 16 channels of the 512-input one and 8 of the 1024-input one (the
+    oracle's cost grows with N^2)."""
+    shapes = [(256, 64, 1024), (512, 128, 1024), (1024, 256, 1024)]
+    checked = [np.arange(64), np.arange(0, 128, 8), np.arange(0, 256, 32)]
+    G = 8
+    s = sv.Service()
+    ids, data = [], []
+    for k, (N, C, T) in enumerate(shapes):
+        ids.append(s.add_stream(N, C, T, ring_gulps=8, integrate_gulps=G, guaranteed=True))
+        data.append(gulps_for(N, C, T, G, seed=80 + k))
+    for q in range(G):                              # interleaved writers
+        for sid, gl in zip(ids, data):
+            assert s.submit(sid, gl[q], q, timeout_ms=20000)
+    for sid, gl, chans in zip(ids, data, checked):
+        r = s.poll(sid, timeout_ms=60000)
+        assert r is not None and r["status"] == 0
+        assert (r["index"], r["gulps"], r["skipped"]) == (0, G, 0)
+        x = np.concatenate(gl, axis=0)
+        want = oracle.correlate(np.ascontiguousarray(x[:, chans, :]))
+        np.testing.assert_array_equal(r["vis"][chans], want)
+        s.release(sid, 0)
+        assert s.stats(sid)["state"] == 0
+    s.close()

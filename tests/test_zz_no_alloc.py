@@ -28,7 +28,15 @@ def xe():
     fn.argtypes = [ctypes.c_void_p, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int,
                    ctypes.c_void_p, ctypes.c_void_p]
     fn.restype = ctypes.c_int
+    chk = xengine.library().xe_correlate_noalloc_check
+    chk.argtypes = [ctypes.c_void_p]
+    chk.restype = ctypes.c_int
     return xengine
+
+
+def check(xe):
+    import torch
+    return xe.library().xe_correlate_noalloc_check(torch.cuda.current_stream().cuda_stream)
 
 
 def noalloc(xe, gulp, out, out_type):
@@ -58,7 +66,7 @@ def test_noalloc_matches_plan_two_calls_in_a_row(xe, out):
         want = plan_result(xe, g, out)
         got = torch.full((C, N * (N + 1) // 2, 2), -7, dtype=dtype, device="cuda")
         assert noalloc(xe, g, got, out_type) == xe.XE_OK
-        torch.cuda.synchronize()
+        assert check(xe) == xe.XE_OK
         np.testing.assert_array_equal(got.cpu().numpy(), want.cpu().numpy())
 
 
@@ -78,3 +86,32 @@ def test_noalloc_rejects_sizes_beyond_its_scratch(xe):
     g = torch.zeros((32, 64, 512), dtype=torch.uint8, device="cuda")  # 64 x 131328 > 2^21
     out = torch.zeros(16, dtype=torch.int32, device="cuda")
     assert noalloc(xe, g, out, xe.XE_OUT_CI32) == xe.XE_ERR_SHAPE
+
+
+def test_noalloc_long_gulp_runs_several_launches(xe):
+    # 40000 samples exceed one launch's exact-float32 bound (32768), so the
+    # call runs two launches, the second adding into the shared scratch;
+    # checked against the CPU oracle, twice in a row
+    import torch
+    import oracle
+    N, C, T = 128, 16, 40000
+    x = synth.voltages(N, C, T, seed=34, random_phase=True)
+    want = oracle.correlate(x)
+    g = torch.from_numpy(x).cuda()
+    for _ in range(2):
+        got = torch.full((C, N * (N + 1) // 2, 2), 5, dtype=torch.int32, device="cuda")
+        assert noalloc(xe, g, got, xe.XE_OUT_CI32) == xe.XE_OK
+        assert check(xe) == xe.XE_OK
+        np.testing.assert_array_equal(got.cpu().numpy().astype(np.int64), want)
+
+
+def test_noalloc_zero_samples_writes_zeros(xe):
+    import torch
+    N, C = 144, 3
+    g = torch.zeros((1, C, N), dtype=torch.uint8, device="cuda")
+    for out_type, dtype in ((xe.XE_OUT_CI32, torch.int32), (xe.XE_OUT_CF32, torch.float32)):
+        got = torch.full((C, N * (N + 1) // 2, 2), 9, dtype=dtype, device="cuda")
+        assert xe.library().xe_correlate_noalloc(g.data_ptr(), 0, C, N, out_type, got.data_ptr(),
+                                                 torch.cuda.current_stream().cuda_stream) == xe.XE_OK
+        assert check(xe) == xe.XE_OK
+        assert int(torch.count_nonzero(got)) == 0
