@@ -146,6 +146,8 @@ class ClockSampler:
         self.lines = []
         self.stop = threading.Event()
         self.thread = None
+        self.nvml_error = None
+        self.sample_error = None
 
     def _handle(self):
         import pynvml
@@ -169,22 +171,25 @@ class ClockSampler:
             except Exception:
                 r = n.nvmlDeviceGetCurrentClocksThrottleReasons(h)
             self.samples.append((float(sm), float(mx), int(r)))
-        except Exception:
-            pass
+        except Exception as e:
+            self.sample_error = f"{type(e).__name__}: {e}"[:200]
 
     def _poll(self):
         while not self.stop.wait(0.002):
             self.sample()
 
     def __enter__(self):
+        self.nvml_error = None
         try:
             self.handle = self._handle()
             self.sample()                       # as the region opens
             self.thread = threading.Thread(target=self._poll, daemon=True)
             self.thread.start()
             return self
-        except Exception:
+        except Exception as e:
             self.handle = None
+            self.nvml_error = f"{type(e).__name__}: {e}"[:200]
+        self._query_once()                      # as the region opens
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
@@ -196,6 +201,15 @@ class ClockSampler:
             self.proc = None
         return self
 
+    def _query_once(self):
+        try:
+            out = subprocess.run(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                                  "--format=csv,noheader,nounits"], capture_output=True, text=True,
+                                 timeout=10).stdout
+            self.lines.extend(l.strip() for l in out.splitlines() if l.strip())
+        except (OSError, subprocess.SubprocessError):
+            pass
+
     def _read(self):
         for line in self.proc.stdout:
             self.lines.append(line.strip())
@@ -206,6 +220,7 @@ class ClockSampler:
             self.stop.set()
             self.thread.join(timeout=1)
             return
+        self._query_once()                      # as the region closes
         if self.proc:
             self.proc.terminate()
             try:
@@ -233,9 +248,12 @@ class ClockSampler:
             for (n, _), v in zip(self.REASONS, parts[3:7]):
                 if v.lower() == "active":
                     reasons.add(n)
-        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx or None,
-                "reasons": sorted(reasons), "samples": len(sm),
-                "source": "nvml" if self.samples else "nvidia-smi"}
+        out = {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx or None,
+               "reasons": sorted(reasons), "samples": len(sm),
+               "source": "nvml" if self.samples else "nvidia-smi"}
+        if self.nvml_error or (self.sample_error and not self.samples):
+            out["nvml_error"] = self.nvml_error or self.sample_error
+        return out
 
 
 def dist_setup():

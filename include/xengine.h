@@ -71,7 +71,9 @@ typedef enum {
     XE_ERR_CUDA = 6,               /* a CUDA runtime/driver call failed */
     XE_ERR_DEVICE_UNSUPPORTED = 7, /* current device is not sm_103 */
     XE_ERR_TIMEOUT = 8,            /* a bounded device-side wait gave up */
-    XE_ERR_BUSY = 9                /* resource in use (serving layer) */
+    XE_ERR_BUSY = 9,               /* resource in use (serving layer) */
+    XE_ERR_DEVICE_INDEX = 10       /* debug build only: a kernel's global index fell outside its
+                                      buffer; the access was skipped (see xe_plan_check) */
 } xe_status;
 
 /* Operand type the contraction runs in.  All three give identical, exact
@@ -404,7 +406,12 @@ XE_API const char *xe_beam_last_error(xe_beam_t beam);
 
 /* Wait for all device work, then report whether any bounded device-side
  * wait of this plan's kernels gave up since the last check
- * (XE_ERR_TIMEOUT; the code is in xe_plan_last_error and is then cleared). */
+ * (XE_ERR_TIMEOUT; the code is in xe_plan_last_error and is then cleared).
+ * In the debug build of the library (libxengine_debug.so, compiled with
+ * XE_DEBUG_CHECKS) the X-engine kernels also check every global index they
+ * store to against its buffer, skip an access outside it and record it
+ * here as XE_ERR_DEVICE_INDEX: the stand-in for a memory checker, without
+ * faulting the GPU. */
 XE_API xe_status xe_plan_check(xe_plan_t plan);
 
 /* Number of kernel launches this plan has enqueued since creation. */

@@ -142,7 +142,7 @@ xe_status enqueue_correlate(xe_plan* p, const uint8_t* d_gulp, int ntime, int ac
   }
   const size_t row_bytes = static_cast<size_t>(p->C) * static_cast<size_t>(p->N);
   if (p->op == XE_OPERAND_INT32_CUDACORE) {
-    cudaError_t e = xe::launch_xcorr_cudacore(d_gulp, ntime, p->C, p->N, acc, accumulate, stream);
+    cudaError_t e = xe::launch_xcorr_cudacore(d_gulp, ntime, p->C, p->N, acc, accumulate, p->d_err, stream);
     if (e != cudaSuccess) return cuda_fail(p, e, "cudacore launch");
     ++p->launches;
     return XE_OK;
@@ -209,6 +209,7 @@ const char* xe_status_string(xe_status s) {
     case XE_ERR_DEVICE_UNSUPPORTED: return "device is not sm_103 (B300)";
     case XE_ERR_TIMEOUT: return "a bounded device-side wait timed out";
     case XE_ERR_BUSY: return "resource busy";
+    case XE_ERR_DEVICE_INDEX: return "device index outside its buffer (debug build)";
   }
   return "unknown status";
 }
@@ -375,10 +376,12 @@ xe_status xe_plan_check(xe_plan_t p) {
   if (e != cudaSuccess) return cuda_fail(p, e, "cudaMemcpy");
   if (err != 0) {
     char buf[96];
-    snprintf(buf, sizeof buf, "device wait timed out (code 0x%x)", err);
+    const bool index = (err & xe::kErrBounds) != 0;
+    snprintf(buf, sizeof buf, index ? "device index check failed (code 0x%x)" : "device wait timed out (code 0x%x)",
+             err);
     p->last_error = buf;
     cudaMemset(p->d_err, 0, sizeof(int));
-    return XE_ERR_TIMEOUT;
+    return index ? XE_ERR_DEVICE_INDEX : XE_ERR_TIMEOUT;
   }
   return XE_OK;
 }

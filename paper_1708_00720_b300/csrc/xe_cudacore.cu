@@ -59,7 +59,7 @@ __device__ __forceinline__ void interleave(uint32_t A0, uint32_t B0, uint32_t A1
 
 __global__ void __launch_bounds__(kThreads)
 xcorr_cudacore_kernel(const uint8_t* __restrict__ x, int T, int C, int N,
-                      int32_t* __restrict__ acc, int accumulate) {
+                      int32_t* __restrict__ acc, int accumulate, int* err) {
   __shared__ __align__(16) uint32_t si[kPairs][kBlk];
   __shared__ __align__(16) uint32_t sj[kPairs][kBlk];
   __shared__ __align__(16) uint32_t sr[kPairs][kBlk];
@@ -150,6 +150,7 @@ xcorr_cudacore_kernel(const uint8_t* __restrict__ x, int T, int C, int N,
         const int gj = bj * kBlk + tj * 4 + b;
         if (gj > gi) continue;
         int2* dst = reinterpret_cast<int2*>(row + 2 * gj);
+        if (!debug_in_bounds(dst, reinterpret_cast<int2*>(acc), C * nbl, err)) continue;
         if (accumulate) {
           const int2 o = *dst;
           *dst = make_int2(o.x + re[a][b], o.y + im[a][b]);
@@ -164,11 +165,11 @@ xcorr_cudacore_kernel(const uint8_t* __restrict__ x, int T, int C, int N,
 }  // namespace cc
 
 cudaError_t launch_xcorr_cudacore(const uint8_t* gulp, int T, int C, int N, int32_t* acc,
-                                  int accumulate, cudaStream_t stream) {
+                                  int accumulate, int* err, cudaStream_t stream) {
   const int nb = (N + cc::kBlk - 1) / cc::kBlk;
   const int npairs = nb * (nb + 1) / 2;
   dim3 grid(npairs, C < 65535 ? C : 65535);
-  cc::xcorr_cudacore_kernel<<<grid, cc::kThreads, 0, stream>>>(gulp, T, C, N, acc, accumulate);
+  cc::xcorr_cudacore_kernel<<<grid, cc::kThreads, 0, stream>>>(gulp, T, C, N, acc, accumulate, err);
   return cudaGetLastError();
 }
 

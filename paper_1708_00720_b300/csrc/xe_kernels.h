@@ -21,7 +21,13 @@ struct TcParams {
   unsigned long long timeout_ns;  // bound on every device-side wait
   int2* split_ws;         // split_workspace_bytes(max_ctas) of scratch for time-sliced units, or nullptr
   int split_parts;        // parts per time-sliced leftover unit, 0: none (set by the launcher)
+  long long acc_pairs;    // int2 elements of acc, C N (N + 1) / 2 (set by the launcher)
+  long long ws_pairs;     // int2 elements of split_ws (set by the launcher)
 };
+
+// Error-word bit of the debug build (XE_DEBUG_CHECKS): a kernel computed a
+// global index outside its buffer; the access was skipped.
+constexpr int kErrBounds = 1 << 9;
 
 // Scratch of the time-sliced leftover units of one launch on at most
 // max_ctas CTAs: one slot per CTA pair, one 128 x 128 int2 tile per CTA.
@@ -44,7 +50,25 @@ cudaError_t launch_xcorr_pair(int eb, const CUtensorMap* tmap_i, const CUtensorM
 
 // Plain CUDA-core correlator (int8 dot products into int32), the baseline.
 cudaError_t launch_xcorr_cudacore(const uint8_t* gulp, int T, int C, int N, int32_t* acc,
-                                  int accumulate, cudaStream_t stream);
+                                  int accumulate, int* err, cudaStream_t stream);
+
+// Index check of a global access in the debug build (XE_DEBUG_CHECKS):
+// element p of an n-element buffer at base.  Outside it, the check sets
+// kErrBounds in *err and the caller skips the access; in the normal build
+// it is always true and compiles away.
+template <typename E>
+__device__ __forceinline__ bool debug_in_bounds(const E* p, const E* base, long long n, int* err) {
+#ifdef XE_DEBUG_CHECKS
+  const long long i = p - base;
+  if (i < 0 || i >= n) {
+    atomicOr(err, kErrBounds);
+    return false;
+  }
+#else
+  (void)p; (void)base; (void)n; (void)err;
+#endif
+  return true;
+}
 
 // 4+4 -> 8+8 unpack of n packed samples (n % 16 == 0 not required).
 cudaError_t launch_unpack(const uint8_t* packed, int8_t* out, long long n, cudaStream_t stream);

@@ -182,5 +182,5 @@ extern "C" XE_API xe_status xe_correlate_noalloc_check(void* stream) {
   if (cudaMemcpy(&err, scratch, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return XE_ERR_CUDA;
   if (err == 0) return XE_OK;
   if (cudaMemset(scratch, 0, sizeof(int)) != cudaSuccess) return XE_ERR_CUDA;
-  return XE_ERR_TIMEOUT;
+  return (err & xe::kErrBounds) ? XE_ERR_DEVICE_INDEX : XE_ERR_TIMEOUT;
 }

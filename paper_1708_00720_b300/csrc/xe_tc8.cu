@@ -47,9 +47,13 @@
 //    im planes.  Input 16g + 2p goes to row 16g + p and input 16g + 2p + 1 to
 //    row 16g + p + 8; the samples of a word follow a fixed permutation of
 //    time within the step, the same on both operands.
-//  * B side (four warps, one 16-input chunk of this CTA's half of J each):
-//    the same transposition, stored K-major with the 128-byte swizzle into
-//    shared memory (64 rows x 128 bytes per plane and stage), rows ordered
+//  * B side (four warps): e4m3 operand B is MN-major with the 64-byte
+//    swizzle, which is the raw half-J tile's own layout (a K row = 64
+//    contiguous input bytes), so each thread unpacks 16-byte chunks in place
+//    (biased re and im bytes at the same N positions) and stores them in K
+//    row kappa(t), the A side's K position of time t: no transposition.
+//    float16 operand B is K-major with the 128-byte swizzle (64 rows x 128
+//    bytes per plane and stage), transposed like the A side, rows ordered
 //    like the A rows.
 //  * MMA (one thread of CTA 0): D_re += A_re B_re^T + A_im B_im^T,
 //                               D_im += A_im B_re^T - A_re B_im^T
@@ -105,7 +109,10 @@ constexpr int kStageBufs = 3;                   // accumulator chunks staged per
 constexpr int kStageRow = 33;                   // words per staged row (padded: conflict-free both ways)
 constexpr int kStageChunk = 32 * kStageRow;     // one 32 x 32 chunk of one half (re or im)
 constexpr int kStageBytes = 4 * 2 * kStageBufs * kStageChunk * 4;  // per warp: re chunks, then im chunks
-constexpr int kSlotInts = 2 * kTile + 2 * kHalf;  // P_I, Q_I (128 each), P_J, Q_J of this CTA's half
+constexpr int kBWarpsSums = 4;                  // B-side warps, each with its own partial sums of J
+// P_I, Q_I (128 each), then per B-side warp P_J, Q_J (64 each) of this CTA's
+// half of J; the column sums are the sums over those warps
+constexpr int kSlotInts = 2 * kTile + kBWarpsSums * 2 * kHalf;
 constexpr int kSumsBytes = 2 * kSlotInts * 4 + 2 * kTile * 4 + 2 * kTile * 4;
 // 2 slots of sums, column corrections (re, im), row and column triangle offsets
 constexpr int kNumBars = 2 * kRawStages + 2 * kOpStages + 3 + 2 + 2 + 1;
@@ -136,6 +143,7 @@ constexpr int kThreads = 32 * (kEpiWarp0 + 4);
 constexpr int kAWarps = 8;
 constexpr int kBWarps = 4;
 constexpr int kStageArrivals = kAWarps + kBWarps;   // per CTA and stage
+static_assert(kBWarpsSums == kBWarps, "one partial-sum block per B-side warp");
 constexpr int kTmemCols = 512;
 constexpr int kTmemA0 = 256;              // A stages: 64 columns each (128 K bytes of re and of im)
 constexpr int kTmemAStage = 64;
@@ -153,7 +161,8 @@ enum ErrCode : int {
 };
 
 struct Smem {
-  uint8_t* op;     // [kOpStages][re, im][64 rows x 128 K bytes]  B planes (this CTA's half)
+  uint8_t* op;     // [kOpStages][re, im][8 KB]  B planes (this CTA's half): e4m3 128 K rows x 64 N
+                   // bytes (MN-major), float16 64 N rows x 128 K bytes (K-major)
   uint8_t* raw;    // [kRawStages][I: kRawTile | J half: kRawHalf]  (Geo<EB>)
   int* stage;      // [4 warps][re, im][kStageBufs][32 rows][kStageRow]
   int* sums;       // [2][kSlotInts]
@@ -283,6 +292,17 @@ __device__ __forceinline__ void tma_prefetch_3d(const void* desc, int x, int y, 
 // better, 0.914 -> 0.907 ms; three, four or eight stages ahead, or
 // prefetching into the next unit, measured no better).
 constexpr int kPrefetch = 1;
+// MN-major operand, 64-byte swizzle: K rows of 64 bytes (64 e4m3 values
+// along N, one swizzle atom wide), 8-row groups 512 B apart.
+__device__ __forceinline__ uint64_t sdesc_mn_sw64(uint32_t saddr) {
+  uint64_t d = 0;
+  d |= static_cast<uint64_t>((saddr >> 4) & 0x3FFFu);
+  d |= 1ull << 16;                                     // leading byte offset: one atom along N, unused
+  d |= static_cast<uint64_t>(512 >> 4) << 32;          // stride byte offset: next 8 K rows
+  d |= 1ull << 46;                                     // descriptor version for tcgen05
+  d |= 4ull << 61;                                     // SWIZZLE_64B
+  return d;
+}
 // K-major operand, 128-byte swizzle: 8-row groups 1024 B apart.
 __device__ __forceinline__ uint64_t sdesc_k_sw128(uint32_t saddr) {
   uint64_t d = 0;
@@ -426,6 +446,15 @@ __device__ __forceinline__ void ldsm_x4_trans(uint32_t addr, uint32_t& d0, uint3
 __device__ __forceinline__ void sts64(uint32_t addr, uint32_t a, uint32_t b) {
   asm volatile("st.shared.v2.u32 [%0], {%1,%2};" ::"r"(addr), "r"(a), "r"(b) : "memory");
 }
+__device__ __forceinline__ void sts128(uint32_t addr, uint32_t a, uint32_t b, uint32_t c, uint32_t d) {
+  asm volatile("st.shared.v4.u32 [%0], {%1,%2,%3,%4};" ::"r"(addr), "r"(a), "r"(b), "r"(c), "r"(d) : "memory");
+}
+__device__ __forceinline__ uint4 lds128(uint32_t addr) {
+  uint4 v;
+  asm volatile("ld.shared.v4.u32 {%0,%1,%2,%3}, [%4];" : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w) : "r"(addr)
+               : "memory");
+  return v;
+}
 // .x2: the re plane (8 columns) and the im plane (the next 8) of one step
 __device__ __forceinline__ void tmem_st_16x256b_x2(uint32_t taddr, uint32_t r0, uint32_t r1, uint32_t r2,
                                                    uint32_t r3, uint32_t r4, uint32_t r5, uint32_t r6,
@@ -455,11 +484,29 @@ __device__ __forceinline__ uint32_t sw128(int k, int q) {
   return static_cast<uint32_t>(k * 128 + ((q ^ (k & 7)) << 4));
 }
 
-// Accumulator row / column -> input offset inside its 128-input tile.
+// Accumulator row -> input offset inside its 128-input tile (the A side's
+// lane order; also the column order of the float16 kernel's B operand).
 __device__ __forceinline__ int lane_to_input(int L) {
   const int r = L & 15;
   return (L & ~15) + (r < 8 ? 2 * r : 2 * (r - 8) + 1);
 }
+// Its inverse: the accumulator row that holds input offset i.
+__device__ __forceinline__ int input_to_lane(int i) {
+  const int r = i & 15;
+  return (i & ~15) + ((r & 1) ? 8 + (r >> 1) : (r >> 1));
+}
+// Accumulator column -> input offset inside the J tile.  The e4m3 kernel's
+// B operand is MN-major in the raw tile's own input order (column n is input
+// n); the float16 kernel's is K-major in the A side's lane order.
+template <int EB>
+__device__ __forceinline__ int col_to_input(int L) {
+  if constexpr (EB == 1) return L;
+  else return lane_to_input(L);
+}
+// K position, within a 32-sample step, of the sample at time t of that step
+// on the A side (the order in which the transposing loads deliver the
+// samples; operand B follows it): kappa(t) = 8 ((t mod 8) / 2) + 2 (t / 8) + t mod 2.
+__device__ __forceinline__ int kappa(int t) { return 8 * ((t & 7) >> 1) + 2 * (t >> 3) + (t & 1); }
 
 // One 32-time x 16-input block of a raw tile (four 8x8 16-bit matrices read
 // transposed by ldmatrix) -> biased e4m3 words of the two
@@ -536,20 +583,22 @@ __device__ __forceinline__ int2 staged(const int* chunk, int r, int k) {
 // The MMAs of one operand stage for the real half of D (WHICH & 1) and/or its
 // imaginary half (WHICH & 2):
 //   D_re += A_re B_re^T + A_im B_im^T,   D_im += A_im B_re^T - A_re B_im^T.
-// A from tensor memory (stage columns at a0), B K-major in shared memory
-// (descriptor bd of the stage's re plane); M = 256 (pair), N = 128.
+// A from tensor memory (stage columns at a0), B in shared memory (descriptor
+// bd of the stage's re plane): e4m3 MN-major (K rows of 64 bytes, bit 16 of
+// the instruction descriptor), float16 K-major; M = 256 (pair), N = 128.
 template <int EB, int WHICH>
 __device__ __forceinline__ void stage_mmas(uint32_t d_re, uint32_t d_im, uint32_t a0, uint64_t bd,
                                            uint32_t acc_first) {
-  constexpr uint32_t id_pos = (1u << 4) | ((128u >> 3) << 17) | ((256u >> 4) << 24);
+  constexpr uint32_t id_pos =
+      (1u << 4) | ((128u >> 3) << 17) | ((256u >> 4) << 24) | (EB == 1 ? (1u << 16) : 0u);
   constexpr uint32_t id_neg = id_pos | (1u << 14);
   constexpr uint32_t kPlaneDesc = kPlane >> 4;   // descriptor address units
   if constexpr (EB == 1) {
-    // per step: A columns re 8 | im 8, B K bytes 32
+    // per step: A columns re 8 | im 8, B K rows 32 (2048 bytes)
 #pragma unroll
     for (int sub = 0; sub < Geo<EB>::kSteps; ++sub) {
       const uint32_t a_re = a0 + 16 * sub, a_im = a_re + 8;
-      const uint64_t b_re = bd + 2 * sub, b_im = bd + kPlaneDesc + 2 * sub;
+      const uint64_t b_re = bd + 128 * sub, b_im = bd + kPlaneDesc + 128 * sub;
       const uint32_t acc0 = sub > 0 ? 1u : acc_first;
       if constexpr ((WHICH & 1) != 0) {
         mma2_f8_tmem_a(d_re, a_re, b_re, id_pos, acc0);
@@ -635,6 +684,9 @@ xcorr_tc8_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant
     tma_prefetch_desc(&tmap);
     tma_prefetch_desc(&tmap_j);
   }
+  // partial-sum blocks a kernel never writes (the float16 B side keeps its
+  // sums in the first block) must read as zero
+  for (int k = tid; k < 2 * kSlotInts; k += kThreads) s.sums[k] = 0;
   if (warp == 0) {
     // one warp of each CTA of the pair allocates together: same columns in both
     asm volatile("tcgen05.alloc.cta_group::2.sync.aligned.shared::cta.b32 [%0], %1;"
@@ -716,7 +768,7 @@ xcorr_tc8_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant
       uint32_t ph = 0;                            // phase of operand slot st
       bool ok = true;
       constexpr uint32_t kSlotDesc = kOpStage >> 4;   // descriptor address units
-      const uint64_t desc0 = sdesc_k_sw128(smem_u32(s.op));
+      const uint64_t desc0 = EB == 1 ? sdesc_mn_sw64(smem_u32(s.op)) : sdesc_k_sw128(smem_u32(s.op));
       const uint32_t d_re = tmem, d_im = tmem + 128;
       for (int it = 0; it < s.sched[0] && ok; ++it, ++ui) {
         const Item w = item_at(s.sched, it);
@@ -865,8 +917,137 @@ xcorr_tc8_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant
       __syncwarp();
       if (lane == 0) mbar_arrive(&s.sums_full[slot]);
     }
-  } else if (b_ordinal(warp) >= 0) {
-    // ====================================================== B side -> shared planes
+  } else if (EB == 1 && b_ordinal(warp) >= 0) {
+    // ====================================================== B side (e4m3) -> MN-major planes
+    // Operand B is MN-major with the 64-byte swizzle: K row k of a step
+    // holds this CTA's 64 J inputs as 64 contiguous bytes, which is the raw
+    // half-J tile's own layout.  Unpacking is therefore element-wise: each
+    // thread takes one 16-byte chunk (16 inputs) of one time row per step,
+    // splits every byte into its biased re and im bytes and stores both at
+    // the same N positions of K row kappa(t), the A side's K position of
+    // that time.  No transposition, one 16-byte load and two 16-byte stores
+    // per chunk.
+    const int g = b_ordinal(warp);
+    const int tau = 32 * g + lane;
+    const int t32 = tau >> 2;                          // time row of this thread within each step
+    const int cl = (tau & 3) ^ ((t32 >> 1) & 3);       // its 16-input chunk (physical chunk tau & 3 of row t32)
+    const int kr = kappa(t32);                         // K row of that time within the step
+    const uint32_t wr_off = static_cast<uint32_t>(kr * 64 + ((cl ^ ((kr >> 1) & 3)) << 4));
+    const uint32_t rdJ = static_cast<uint32_t>(t32 * 64 + ((tau & 3) << 4));
+    // when I == J the half comes from the I tile (128-byte rows, 128-byte swizzle)
+    const uint32_t rdI = static_cast<uint32_t>(t32 * 128 + (((4 * static_cast<int>(rank) + cl) ^ (t32 & 7)) << 4));
+    int sit = 0, ui = 0;
+    bool ok = true;
+    for (int it = 0; it < s.sched[0] && ok; ++it, ++ui) {
+      const Item w = item_at(s.sched, it);
+      const Unit t = decode_unit(w.u, per_chan, nt, rank);
+      const bool own_diag = (t.ti == t.tj);
+      // sums of the biased parts of the chunk's 16 inputs: byte lanes (at most
+      // 4 x 4 x 15 = 240 between folds), then 16-bit lanes ([2k]: bytes 0 and
+      // 2 of word k, [2k + 1]: bytes 1 and 3; at most 15 T / 32 per thread)
+      uint32_t bP[4] = {0u, 0u, 0u, 0u}, bQ[4] = {0u, 0u, 0u, 0u};
+      uint32_t hP[8] = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u}, hQ[8] = {0u, 0u, 0u, 0u, 0u, 0u, 0u, 0u};
+      int since_fold = 0;
+      for (int ks = w.k0; ks < w.k1; ks += G::kSteps, ++sit) {
+        const int rst = sit % kRawStages, ost = sit % kOpStages;
+        if (!wait_or_abort(&s.raw_full[rst], (sit / kRawStages) & 1, lim, abort_flag)) {
+          fail(s, prm.err, kErrWaitRawFull);
+          ok = false;
+          break;
+        }
+        const uint32_t raw_s = smem_u32(s.raw + rst * G::kRawStage);
+        const uint32_t src = own_diag ? raw_s + rdI : raw_s + G::kRawTile + rdJ;
+        const uint32_t sstep = own_diag ? kRawSub : kRawSub / 2;
+        uint4 v[G::kSteps];
+#pragma unroll
+        for (int sub = 0; sub < G::kSteps; ++sub) v[sub] = lds128(src + sub * sstep);
+        if (!wait_or_abort(&s.op_empty[ost], ((sit / kOpStages) & 1) ^ 1, lim, abort_flag)) {
+          fail(s, prm.err, kErrWaitOpEmpty);
+          ok = false;
+          break;
+        }
+        const uint32_t dst = smem_u32(s.op + ost * kOpStage) + wr_off;
+#pragma unroll
+        for (int sub = 0; sub < G::kSteps; ++sub) {
+          const uint32_t x[4] = {v[sub].x, v[sub].y, v[sub].z, v[sub].w};
+          uint32_t re[4], im[4];
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            re[k] = biased_re(x[k]);
+            im[k] = biased_im(x[k]);
+            bP[k] += re[k];
+            bQ[k] += im[k];
+          }
+          sts128(dst + sub * (32 * 64), re[0], re[1], re[2], re[3]);
+          sts128(dst + kPlane + sub * (32 * 64), im[0], im[1], im[2], im[3]);
+        }
+        fence_proxy_async_smem();
+        __syncwarp();
+        if (lane == 0) {
+          mbar_arrive(&s.op_full[ost]);
+          mbar_arrive(&s.raw_empty[rst]);
+        }
+        if (++since_fold == 4 || ks + G::kSteps >= w.k1) {
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            hP[2 * k] += bP[k] & 0x00FF00FFu;
+            hP[2 * k + 1] += (bP[k] >> 8) & 0x00FF00FFu;
+            hQ[2 * k] += bQ[k] & 0x00FF00FFu;
+            hQ[2 * k + 1] += (bQ[k] >> 8) & 0x00FF00FFu;
+            bP[k] = bQ[k] = 0u;
+          }
+          since_fold = 0;
+        }
+      }
+      if (!ok) break;
+      // The 8 lanes of a warp that share a chunk differ by XOR 4, 9 and 18.
+      // Two levels in 16-bit lanes (at most 4 x 15 T / 32 < 2^16 for T <=
+      // 32768), then the values in 32 bits and the last level.
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        hP[k] += __shfl_xor_sync(0xFFFFFFFFu, hP[k], 4);
+        hQ[k] += __shfl_xor_sync(0xFFFFFFFFu, hQ[k], 4);
+        hP[k] += __shfl_xor_sync(0xFFFFFFFFu, hP[k], 9);
+        hQ[k] += __shfl_xor_sync(0xFFFFFFFFu, hQ[k], 9);
+      }
+      int P[16], Q[16];   // input 4k + b of the chunk
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        P[4 * k + 0] = static_cast<int>(hP[2 * k] & 0xFFFFu);
+        P[4 * k + 1] = static_cast<int>(hP[2 * k + 1] & 0xFFFFu);
+        P[4 * k + 2] = static_cast<int>(hP[2 * k] >> 16);
+        P[4 * k + 3] = static_cast<int>(hP[2 * k + 1] >> 16);
+        Q[4 * k + 0] = static_cast<int>(hQ[2 * k] & 0xFFFFu);
+        Q[4 * k + 1] = static_cast<int>(hQ[2 * k + 1] & 0xFFFFu);
+        Q[4 * k + 2] = static_cast<int>(hQ[2 * k] >> 16);
+        Q[4 * k + 3] = static_cast<int>(hQ[2 * k + 1] >> 16);
+      }
+#pragma unroll
+      for (int e = 0; e < 16; ++e) {
+        P[e] += __shfl_xor_sync(0xFFFFFFFFu, P[e], 18);
+        Q[e] += __shfl_xor_sync(0xFFFFFFFFu, Q[e], 18);
+      }
+      const int slot = ui & 1;
+      if (!wait_or_abort(&s.sums_empty[slot], ((ui >> 1) & 1) ^ 1, lim, abort_flag)) {
+        fail(s, prm.err, kErrWaitSumsEmpty);
+        break;
+      }
+      int* sl = s.sums + slot * kSlotInts + 2 * kTile + g * 2 * kHalf;   // this warp's block
+      if (lane < 4) {   // lane c holds chunk c (lane >> 3 == 0)
+#pragma unroll
+        for (int e = 0; e < 16; ++e) {
+          sl[16 * lane + e] = P[e];
+          sl[kHalf + 16 * lane + e] = Q[e];
+        }
+      }
+      __syncwarp();
+      if (lane == 0) {
+        mbar_arrive(&s.sums_full[slot]);
+        arrive_at(&s.sums_full[slot], peer);   // the partner's epilogue reads this half too
+      }
+    }
+  } else if (EB == 2 && b_ordinal(warp) >= 0) {
+    // ====================================================== B side (float16) -> K-major planes
     const int g = b_ordinal(warp);             // 16-input chunk within this CTA's half of J
     const int q = 4 * static_cast<int>(rank) + g;  // the same chunk within the J tile
     const int pj = lane >> 2;
@@ -909,26 +1090,17 @@ xcorr_tc8_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant
           const Words w = unpack_words(dv[sub], ps.bP, ps.bQ);
           // K-major rows n0 and n0 + 8 (same swizzle phase), the same K
           // positions as the A side
-          if constexpr (EB == 1) {
-            const int kb = 32 * sub + 8 * kq;
-            const uint32_t off = static_cast<uint32_t>(n0 * 128 + (((kb >> 4) ^ (n0 & 7)) << 4) + (kb & 15));
-            sts64(opB + off, w.re0, w.re1);
-            sts64(opB + off + 8 * 128, w.re2, w.re3);
-            sts64(opB + kPlane + off, w.im0, w.im1);
-            sts64(opB + kPlane + off + 8 * 128, w.im2, w.im3);
-          } else {
-            const int kb0 = 64 * sub + 8 * kq, kb1 = kb0 + 32;
-            const uint32_t o0 = static_cast<uint32_t>(n0 * 128 + (((kb0 >> 4) ^ (n0 & 7)) << 4) + (kb0 & 15));
-            const uint32_t o1 = static_cast<uint32_t>(n0 * 128 + (((kb1 >> 4) ^ (n0 & 7)) << 4) + (kb1 & 15));
-            sts64(opB + o0, f16_lo(w.re0), f16_hi(w.re0));
-            sts64(opB + o1, f16_lo(w.re1), f16_hi(w.re1));
-            sts64(opB + o0 + 8 * 128, f16_lo(w.re2), f16_hi(w.re2));
-            sts64(opB + o1 + 8 * 128, f16_lo(w.re3), f16_hi(w.re3));
-            sts64(opB + kPlane + o0, f16_lo(w.im0), f16_hi(w.im0));
-            sts64(opB + kPlane + o1, f16_lo(w.im1), f16_hi(w.im1));
-            sts64(opB + kPlane + o0 + 8 * 128, f16_lo(w.im2), f16_hi(w.im2));
-            sts64(opB + kPlane + o1 + 8 * 128, f16_lo(w.im3), f16_hi(w.im3));
-          }
+          const int kb0 = 64 * sub + 8 * kq, kb1 = kb0 + 32;
+          const uint32_t o0 = static_cast<uint32_t>(n0 * 128 + (((kb0 >> 4) ^ (n0 & 7)) << 4) + (kb0 & 15));
+          const uint32_t o1 = static_cast<uint32_t>(n0 * 128 + (((kb1 >> 4) ^ (n0 & 7)) << 4) + (kb1 & 15));
+          sts64(opB + o0, f16_lo(w.re0), f16_hi(w.re0));
+          sts64(opB + o1, f16_lo(w.re1), f16_hi(w.re1));
+          sts64(opB + o0 + 8 * 128, f16_lo(w.re2), f16_hi(w.re2));
+          sts64(opB + o1 + 8 * 128, f16_lo(w.re3), f16_hi(w.re3));
+          sts64(opB + kPlane + o0, f16_lo(w.im0), f16_hi(w.im0));
+          sts64(opB + kPlane + o1, f16_lo(w.im1), f16_hi(w.im1));
+          sts64(opB + kPlane + o0 + 8 * 128, f16_lo(w.im2), f16_hi(w.im2));
+          sts64(opB + kPlane + o1 + 8 * 128, f16_lo(w.im3), f16_hi(w.im3));
         }
         fence_proxy_async_smem();
         __syncwarp();
@@ -970,7 +1142,8 @@ xcorr_tc8_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant
     // skips work.
     const int quad = warp & 3;
     const int L = 32 * quad + lane;                 // TMEM lane = accumulator row; also a column index
-    const int il = lane_to_input(L);                // input offset of row / column L in its tile
+    const int il = lane_to_input(L);                // input offset of row L in its tile
+    const int jl = col_to_input<EB>(L);             // input offset of column L in its tile
     const long long nbl = static_cast<long long>(prm.N) * (prm.N + 1) / 2;
     int* const sre = s.stage + quad * 2 * kStageBufs * kStageChunk;   // this warp's staged real parts
     int* const sim = sre + kStageBufs * kStageChunk;                   // and imaginary parts
@@ -991,24 +1164,31 @@ xcorr_tc8_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant
         // bias corrections of this lane's row and of column L (see unbias)
         row_re = static_cast<float>(-8 * (sl[il] + sl[kTile + il]) + 128 * T_pad);
         row_im = static_cast<float>(8 * (sl[il] - sl[kTile + il]));
-        // column L is J input il; its half (L / 64) is held by CTA L / 64
+        // column L is J input jl; its half (L / 64) is held by CTA L / 64,
+        // whose B-side warps each left partial sums in a block of their own
         const uint32_t holder = static_cast<uint32_t>(L >> 6);
-        const int jo = il - kHalf * static_cast<int>(holder);
+        const int jo = jl - kHalf * static_cast<int>(holder);
         const int* pq = sl + 2 * kTile;
-        const int pjv = holder == rank ? pq[jo] : ld_peer(pq + jo, holder);
-        const int qjv = holder == rank ? pq[kHalf + jo] : ld_peer(pq + kHalf + jo, holder);
+        int pjv = 0, qjv = 0;
+#pragma unroll
+        for (int b = 0; b < kBWarps; ++b) {
+          const int* blk = pq + b * 2 * kHalf;
+          pjv += holder == rank ? blk[jo] : ld_peer(blk + jo, holder);
+          qjv += holder == rank ? blk[kHalf + jo] : ld_peer(blk + kHalf + jo, holder);
+        }
         s.colcorr[L] = static_cast<float>(-8 * (pjv + qjv));
         s.colcorr[kTile + L] = static_cast<float>(-8 * (pjv - qjv));
       }
       if (w.lo < 0) {
         // packed-triangle offsets of row L's and column L's inputs (N <= 8192 fits int)
-        const int gi = t.ti * kTile + il, gj = t.tj * kTile + il;
+        const int gi = t.ti * kTile + il, gj = t.tj * kTile + jl;
         s.rowoff[L] = gi < prm.N ? gi * (gi + 1) / 2 : 0;
         s.coloff[L] = gj < prm.N ? gj * (gj + 1) / 2 : 0;
       } else {
-        // a part: rows of the compact workspace tile
+        // a part: rows of the compact workspace tile, in accumulator-row
+        // order (a transposed part's rows are J inputs: row input_to_lane(jl))
         s.rowoff[L] = L * kTile;
-        s.coloff[L] = L * kTile;
+        s.coloff[L] = input_to_lane(jl) * kTile;
       }
       asm volatile("bar.sync 1, 128;" ::: "memory");
       if (lane == 0) {   // this slot's own sums and the partner's half of J have been read
@@ -1059,6 +1239,9 @@ xcorr_tc8_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant
             w.lo < 0 ? reinterpret_cast<int2*>(prm.acc) + static_cast<long long>(t.c) * nbl
                      : prm.split_ws + (static_cast<long long>(2 * cl + rank) * kSplitTile -
                                        (t.transposed ? t.ti : t.tj) * kTile);
+        // the buffer written, for the debug build's index checks
+        const int2* const wbase = w.lo < 0 ? reinterpret_cast<const int2*>(prm.acc) : prm.split_ws;
+        const long long wlen = w.lo < 0 ? prm.acc_pairs : prm.ws_pairs;
         // a tile strictly below the diagonal and inside N needs no checks
         const bool full = !t.transposed && t.ti > t.tj && t.ti * kTile + kTile <= prm.N;
         const bool tfull = t.transposed && t.tj * kTile + kTile <= prm.N;
@@ -1077,14 +1260,16 @@ xcorr_tc8_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant
           if (!t.transposed) {
             // 32 rows x 32 baselines: each row is 256 contiguous bytes (lanes
             // permuted); row r's corrections come from lane r
-            const int gj = t.tj * kTile + lane_to_input(cc + lane);
+            const int gj = t.tj * kTile + col_to_input<EB>(cc + lane);
             const float cre = s.colcorr[cc + lane], cim = s.colcorr[kTile + cc + lane];
             int2* accj = acc + gj;
             if (full && !accumulate) {
 #pragma unroll 4
               for (int r = 0; r < 32; ++r) {
                 const float rre = __shfl_sync(0xFFFFFFFFu, row_re, r), rim = __shfl_sync(0xFFFFFFFFu, row_im, r);
-                accj[ro[r]] = unbias<EB>(staged(sb, r, lane), rre, rim, cre, cim);
+                int2* dst = accj + ro[r];
+                if (debug_in_bounds(dst, wbase, wlen, prm.err))
+                  *dst = unbias<EB>(staged(sb, r, lane), rre, rim, cre, cim);
               }
             } else if (full) {
 #pragma unroll 4
@@ -1092,8 +1277,10 @@ xcorr_tc8_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant
                 const float rre = __shfl_sync(0xFFFFFFFFu, row_re, r), rim = __shfl_sync(0xFFFFFFFFu, row_im, r);
                 const int2 v = unbias<EB>(staged(sb, r, lane), rre, rim, cre, cim);
                 int2* dst = accj + ro[r];
-                const int2 o = *dst;
-                *dst = make_int2(o.x + v.x, o.y + v.y);
+                if (debug_in_bounds(dst, wbase, wlen, prm.err)) {
+                  const int2 o = *dst;
+                  *dst = make_int2(o.x + v.x, o.y + v.y);
+                }
               }
             } else {
 #pragma unroll 4
@@ -1103,6 +1290,7 @@ xcorr_tc8_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant
                 if (gi < prm.N && gj <= gi) {
                   const int2 v = unbias<EB>(staged(sb, r, lane), rre, rim, cre, cim);
                   int2* dst = accj + ro[r];
+                  if (!debug_in_bounds(dst, wbase, wlen, prm.err)) continue;
                   if (accumulate) {
                     const int2 o = *dst;
                     *dst = make_int2(o.x + v.x, o.y + v.y);
@@ -1119,10 +1307,11 @@ xcorr_tc8_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant
             int2* acci = acc + gI;
 #pragma unroll 4
             for (int k = 0; k < 32; ++k) {
-              if (tfull || t.tj * kTile + lane_to_input(cc + k) < prm.N) {
+              if (tfull || t.tj * kTile + col_to_input<EB>(cc + k) < prm.N) {
                 const int2 v = unbias<EB>(staged(sb, lane, k), row_re, row_im, s.colcorr[cc + k],
                                           s.colcorr[kTile + cc + k]);
                 int2* dst = acci + s.coloff[cc + k];
+                if (!debug_in_bounds(dst, wbase, wlen, prm.err)) continue;
                 if (accumulate) {
                   const int2 o = *dst;
                   *dst = make_int2(o.x + v.x, o.y - v.y);
@@ -1172,6 +1361,8 @@ struct CombineParams {
   int N, nt, per_chan, units, ncl, q, accumulate;
   int32_t* acc;
   const int2* ws;
+  long long acc_pairs, ws_pairs;   // element counts, for the debug build's index checks
+  int* err;
 };
 
 __global__ void __launch_bounds__(256) split_combine_kernel(const CombineParams p) {
@@ -1189,6 +1380,7 @@ __global__ void __launch_bounds__(256) split_combine_kernel(const CombineParams 
     const int2* src = p.ws + static_cast<long long>(2 * c + rank) * kSplitTile + a * kTile;
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
+      if (!debug_in_bounds(src + lane + 32 * k, p.ws, p.ws_pairs, p.err)) continue;
       const int2 v = src[lane + 32 * k];
       sx[k] += v.x;
       sy[k] += v.y;
@@ -1199,6 +1391,7 @@ __global__ void __launch_bounds__(256) split_combine_kernel(const CombineParams 
     const int gj = Ct * kTile + lane + 32 * k;
     if (gj > gi) break;
     int2* d = orow + gj;
+    if (!debug_in_bounds(d, reinterpret_cast<const int2*>(p.acc), p.acc_pairs, p.err)) continue;
     if (p.accumulate) {
       const int2 o = *d;
       *d = make_int2(o.x + sx[k], o.y + sy[k]);
@@ -1242,6 +1435,8 @@ cudaError_t launch_pair(const CUtensorMap* tmap_i, const CUtensorMap* tmap_j, Tc
   if (units < clusters) clusters = units;
   if (clusters < 1) clusters = 1;
   prm.split_parts = prm.split_ws ? tc8::split_parts(units, clusters, prm.nks, tc8::Geo<EB>::kSteps) : 0;
+  prm.acc_pairs = static_cast<long long>(prm.C) * prm.N * (prm.N + 1) / 2;
+  prm.ws_pairs = prm.split_ws ? static_cast<long long>(split_workspace_bytes(max_ctas) / sizeof(int2)) : 0;
   tc8::xcorr_tc8_kernel<EB><<<static_cast<int>(2 * clusters), tc8::kThreads, smem, stream>>>(*tmap_i, *tmap_j, prm);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
@@ -1257,6 +1452,9 @@ cudaError_t launch_pair(const CUtensorMap* tmap_i, const CUtensorMap* tmap_j, Tc
     q.accumulate = prm.accumulate;
     q.acc = prm.acc;
     q.ws = prm.split_ws;
+    q.acc_pairs = prm.acc_pairs;
+    q.ws_pairs = prm.ws_pairs;
+    q.err = prm.err;
     const int L = static_cast<int>(units % clusters);
     tc8::split_combine_kernel<<<dim3(2 * L, tc8::kTile / 8), 256, 0, stream>>>(q);
     e = cudaGetLastError();

@@ -27,6 +27,7 @@ XE_ERR_CUDA = 6
 XE_ERR_DEVICE_UNSUPPORTED = 7
 XE_ERR_TIMEOUT = 8
 XE_ERR_BUSY = 9
+XE_ERR_DEVICE_INDEX = 10
 
 XE_OPERAND_FP8_E4M3 = 0
 XE_OPERAND_FP16 = 1
@@ -51,10 +52,10 @@ class XEngineError(RuntimeError):
         super().__init__(msg)
 
 
-def _load() -> ctypes.CDLL:
-    path = _build.LIB
-    if not os.path.exists(path) or _build.is_stale():
-        _build.build()
+def _load(debug: bool = False) -> ctypes.CDLL:
+    path = _build.LIB_DEBUG if debug else _build.LIB
+    if not os.path.exists(path) or _build.is_stale(path):
+        _build.build(debug=debug)
     lib = ctypes.CDLL(path)
     P, I, LL = ctypes.c_void_p, ctypes.c_int, ctypes.c_longlong
     sigs = {
@@ -99,6 +100,20 @@ def header_functions() -> list[str]:
 
 def library() -> ctypes.CDLL:
     return _lib
+
+
+_debug_lib = None
+
+
+def debug_library() -> ctypes.CDLL:
+    """The index-checked build (XE_DEBUG_CHECKS) of the same library, loaded
+    beside the normal one: its X-engine kernels check every global store
+    against its buffer and report a miss through xe_plan_check as
+    XE_ERR_DEVICE_INDEX instead of writing outside it."""
+    global _debug_lib
+    if _debug_lib is None:
+        _debug_lib = _load(debug=True)
+    return _debug_lib
 
 
 def xe_status_string(status: int) -> str:
