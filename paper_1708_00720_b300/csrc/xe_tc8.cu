@@ -136,7 +136,7 @@ struct Geo {
 // epilogue warps need their warp index = TMEM lane quadrant (mod 4).
 //   0: TMA I tiles   1: MMA issuer (CTA 0)   2: TMA J tiles
 //   4-7, 12-15: A side (quadrant w % 4, chunk (w >> 3) & 1)
-//   3, 8, 10, 11: B side (chunk 0..3 of this CTA's half of J)   9: idle
+//   3, 8, 10, 11: B side   9: second stage forwarder (CTA 1), idle in CTA 0
 //   16-19: epilogue
 constexpr int kEpiWarp0 = 16;
 constexpr int kThreads = 32 * (kEpiWarp0 + 4);
@@ -471,6 +471,18 @@ __device__ __forceinline__ void tmem_st_16x256b_x4(uint32_t taddr, const uint32_
                  "r"(r[8]), "r"(r[9]), "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15])
                : "memory");
 }
+// Release a raw stage as soon as this warp's loads from it have returned:
+// the XOR reads every loaded register (so the loads have completed), the
+// empty asm keeps it ahead of the arrive, and lane 0 arrives for the warp.
+template <int NW>
+__device__ __forceinline__ void release_raw_after_loads(const uint32_t* words, uint64_t* bar, int lane) {
+  uint32_t dep = 0;
+#pragma unroll
+  for (int k = 0; k < NW; ++k) dep ^= words[k];
+  asm volatile("" ::"r"(dep));
+  __syncwarp();
+  if (lane == 0) mbar_arrive(bar);
+}
 __device__ __forceinline__ void tmem_st_wait() {
   asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
 }
@@ -736,17 +748,21 @@ xcorr_tc8_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant
       for (int k = rit - 1; k >= 0 && k > rit - 1 - kRawStages; --k)
         mbar_wait(&s.raw_full[k % kRawStages], (k / kRawStages) & 1, lim);
     }
-  } else if (warp == 1 && rank == 1) {
-    // ====================================================== stage forwarder (CTA 1)
-    // A release at cluster scope costs the arriving thread several hundred
-    // cycles, so CTA 1's producers arrive on their local barrier and this
-    // thread alone tells CTA 0 that CTA 1's half of a stage is ready.
+  } else if ((warp == 1 || warp == 9) && rank == 1) {
+    // ====================================================== stage forwarders (CTA 1)
+    // A release at cluster scope costs the arriving thread ~1100 cycles
+    // (measured), so CTA 1's producers arrive on their local barrier and two
+    // threads, in warps 1 and 9, tell CTA 0 that CTA 1's half of a stage is
+    // ready: warp 1 forwards the even stages, warp 9 the odd ones.  One
+    // forwarder was busy 93 % of the kernel and paced the stages.
     if (lane == 0) {
+      const int fwd = warp == 9 ? 1 : 0;
       int sit = 0;
       bool ok = true;
       for (int it = 0; it < s.sched[0] && ok; ++it) {
         const Item w = item_at(s.sched, it);
         for (int ks = w.k0; ks < w.k1; ks += G::kSteps, ++sit) {
+          if ((sit & 1) != fwd) continue;
           const int st = sit % kOpStages;
           if (!wait_or_abort(&s.op_full[st], (sit / kOpStages) & 1, lim, abort_flag)) {
             fail(s, prm.err, kErrWaitOpFull);
@@ -865,6 +881,10 @@ xcorr_tc8_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant
 #pragma unroll
         for (int sub = 0; sub < G::kSteps; ++sub)
           ldsm_x4_trans(rawI_s + sub * kRawSub + sw128(lane, ch), dv[sub][0], dv[sub][1], dv[sub][2], dv[sub][3]);
+        // the raw stage goes back to the TMA producers before this warp waits
+        // for its operand slot (raw tiles arrive with L2 latency; two raw
+        // stages leave little slack)
+        release_raw_after_loads<4 * G::kSteps>(&dv[0][0], &s.raw_empty[rst], lane);
         if (!wait_or_abort(&s.op_empty[ost], ((sit / kOpStages) & 1) ^ 1, lim, abort_flag)) {
           fail(s, prm.err, kErrWaitOpEmpty);
           ok = false;
@@ -889,10 +909,7 @@ xcorr_tc8_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant
         tmem_st_wait();
         tc_fence_before();
         __syncwarp();
-        if (lane == 0) {
-          mbar_arrive(&s.op_full[ost]);
-          mbar_arrive(&s.raw_empty[rst]);
-        }
+        if (lane == 0) mbar_arrive(&s.op_full[ost]);
         if (++since_fold == 2 || ks + G::kSteps >= w.k1) {
           ps.fold();
           since_fold = 0;
@@ -961,6 +978,7 @@ xcorr_tc8_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant
         uint4 v[G::kSteps];
 #pragma unroll
         for (int sub = 0; sub < G::kSteps; ++sub) v[sub] = lds128(src + sub * sstep);
+        release_raw_after_loads<4 * G::kSteps>(&v[0].x, &s.raw_empty[rst], lane);
         if (!wait_or_abort(&s.op_empty[ost], ((sit / kOpStages) & 1) ^ 1, lim, abort_flag)) {
           fail(s, prm.err, kErrWaitOpEmpty);
           ok = false;
@@ -983,10 +1001,7 @@ xcorr_tc8_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant
         }
         fence_proxy_async_smem();
         __syncwarp();
-        if (lane == 0) {
-          mbar_arrive(&s.op_full[ost]);
-          mbar_arrive(&s.raw_empty[rst]);
-        }
+        if (lane == 0) mbar_arrive(&s.op_full[ost]);
         if (++since_fold == 4 || ks + G::kSteps >= w.k1) {
 #pragma unroll
           for (int k = 0; k < 4; ++k) {
@@ -1079,6 +1094,7 @@ xcorr_tc8_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant
 #pragma unroll
         for (int sub = 0; sub < G::kSteps; ++sub)
           ldsm_x4_trans(rowJ + sub * subJ, dv[sub][0], dv[sub][1], dv[sub][2], dv[sub][3]);
+        release_raw_after_loads<4 * G::kSteps>(&dv[0][0], &s.raw_empty[rst], lane);
         if (!wait_or_abort(&s.op_empty[ost], ((sit / kOpStages) & 1) ^ 1, lim, abort_flag)) {
           fail(s, prm.err, kErrWaitOpEmpty);
           ok = false;
@@ -1104,10 +1120,7 @@ xcorr_tc8_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant
         }
         fence_proxy_async_smem();
         __syncwarp();
-        if (lane == 0) {
-          mbar_arrive(&s.op_full[ost]);
-          mbar_arrive(&s.raw_empty[rst]);
-        }
+        if (lane == 0) mbar_arrive(&s.op_full[ost]);
         if (++since_fold == 2 || ks + G::kSteps >= w.k1) {
           ps.fold();
           since_fold = 0;
