@@ -553,7 +553,7 @@ def run_calib(args, world, rank, local, pg, dev):
         line = {
             "metric": CALIB_METRIC, "value": value, "unit": "G baselines/s", "n_gpus": world,
             "steps": args.steps, "warmup": max(args.warmup, 3), "ms_per_step": ms,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32 (chi^2: compensated f32 per warp, f64 across warps)",
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32 (chi^2: compensated f32, f64 only over the last 8 partials)",
             "data": "synthetic (seeded gains, 5-source sky model, noisy V_obs)",
             "config": {"workload": WORKLOADS["calib"][1], "n_input": N, "n_chan": C, "weights": "ones (read)",
                        "l2": f"inputs ({(m.nbytes + v.nbytes + w.nbytes) >> 20} MiB) exceed L2 (126 MB); no flush",

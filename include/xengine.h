@@ -238,7 +238,8 @@ XE_API xe_status xe_correlate_noalloc_check(void *stream);
  * (n_input + 1) / 2] in the visibility layout above; d_w float32 weights in
  * the same layout, or NULL for all ones.  Complex pointers must be 8-byte
  * aligned.  Per-baseline terms are float32; chi^2 is summed in float32 with a
- * compensation term per thread and warp, and the per-warp sums in float64; both
+ * compensation term (per thread, per warp and over the warps) and in float64
+ * only over the final 8 partial totals; both
  * results are deterministic.  The object owns its scratch (per-CTA chi^2
  * partials and the adjoint's partial sums); calls on one object must not
  * overlap.  Errors: XE_ERR_INVALID_ARG for a NULL handle or required pointer

@@ -11,9 +11,9 @@
 // bytes each, and w, 4 bytes, are read once).  A small second kernel
 // (calib_combine_kernel) adds the partials in a fixed order.  Per-baseline
 // terms are float32.  chi^2 is summed in float32 with a compensation term
-// (TwoSum, Knuth) per thread and across the warp, so the pass kernel holds
-// no float64; only the final reduction of the per-warp (sum, compensation)
-// pairs in calib_combine_kernel is float64.  The gradient is summed in
+// (TwoSum, Knuth) per thread, across the warp and over the warps' partials
+// in calib_combine_kernel; float64 is used only for the final sum of that
+// kernel's 8 warp totals.  The gradient is summed in
 // float32.  Every summation order is fixed by the problem size and the grid,
 // so both results are deterministic.
 #include <cuda_runtime.h>
@@ -452,26 +452,31 @@ calib_combine_kernel(Geometry G, Scratch sc, const double* __restrict__ scale, f
     grad[t] = make_float2(f * acc.x, f * acc.y);
   }
   if (chisq && blockIdx.x == gridDim.x - 1) {
-    __shared__ double red[8];
-    double acc = 0.0;
+    // The per-warp (sum, compensation) pairs are added with the same
+    // compensated float32 sum, per thread and across each warp; float64
+    // appears only in the last step, over the 8 warps' pairs (B300's float64
+    // rate is a small fraction of its float32 rate: converting every pair
+    // here cost ~5 us of one SM).
+    __shared__ float2 red[8];
+    CompSum acc;
     for (int q0 = threadIdx.x; q0 < G.W; q0 += 8 * 256) {
-      double p[8];
+      float2 p[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) p[u] = q0 + u * 256 < G.W ? __ldcg(sc.chi_part + q0 + u * 256) : make_float2(0.f, 0.f);
 #pragma unroll
       for (int u = 0; u < 8; ++u) {
-        const float2 e = q0 + u * 256 < G.W ? __ldcg(sc.chi_part + q0 + u * 256) : make_float2(0.f, 0.f);
-        p[u] = static_cast<double>(e.x) + static_cast<double>(e.y);
+        acc.c += p[u].y;
+        acc.add(p[u].x);
       }
-#pragma unroll
-      for (int u = 0; u < 8; ++u) acc += p[u];
     }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xFFFFFFFFu, acc, o);
-    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+    for (int o = 16; o > 0; o >>= 1) acc.add_lane(o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = make_float2(acc.s, acc.c);
     __syncthreads();
     if (threadIdx.x == 0) {
-      double r = red[0];
+      double r = 0.0;
 #pragma unroll
-      for (int q = 1; q < 8; ++q) r += red[q];
+      for (int q = 0; q < 8; ++q) r += static_cast<double>(red[q].x) + static_cast<double>(red[q].y);
       *chisq = r;
     }
   }
