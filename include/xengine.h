@@ -150,6 +150,28 @@ XE_API xe_status xe_correlate(xe_plan_t plan, const uint8_t *d_gulp, int ntime,
  * type = the plan's xe_out).  d_vis must be 8-byte aligned. */
 XE_API xe_status xe_integrate(xe_plan_t plan, void *d_vis, void *stream);
 
+/*
+ * Several independent correlations in ONE launch: plan k correlates
+ * d_gulps[k][ntime[k]][C_k][N_k] into its own accumulator exactly as
+ * xe_correlate(plans[k], d_gulps[k], ntime[k], accumulate[k], stream)
+ * would, while one persistent grid of CTA pairs works through the
+ * concatenated tile-pair units of all problems.  This is how the streaming
+ * service batches the gulps of different streams (arrays of different
+ * sizes) that are ready at the same time ("Memory management and ring
+ * buffers": every reader of a ring processes its own span of data; here
+ * several readers share one launch).
+ *  - 1 <= n <= 8 distinct plans, all XE_OPERAND_FP8_E4M3 and created on the
+ *    current device; each ntime[k] <= 32768 (one launch per problem:
+ *    XE_ERR_SHAPE beyond) and within its plan's max_ntime and integration
+ *    bounds; the other rules and errors as for xe_correlate.  Nothing is
+ *    launched if any problem fails a check.
+ *  - Each plan's sample counter and launch count are updated as by
+ *    xe_correlate; a device wait that times out is reported by
+ *    xe_plan_check of every plan of the batch.
+ */
+XE_API xe_status xe_correlate_batch(int n, const xe_plan_t *plans, const uint8_t *const *d_gulps,
+                                    const int *ntime, const int *accumulate, void *stream);
+
 /* A one-gulp integration in one call (sections "Some included blocks" and
  * "Memory management and ring buffers": correlate, accumulate and emit when
  * the integration is a single gulp): the visibilities of this gulp alone,
@@ -290,6 +312,11 @@ XE_API xe_status xe_calib_scale(xe_calib_t calib, const float *d_in, const doubl
  * gulps that never arrived).  Committed gulps are copied to the device ring
  * at once; pending gulps that are contiguous in the ring are correlated in
  * one launch whenever the stream has fewer than two launches in flight.
+ * When several e4m3 streams have such runs ready at the same time (each of
+ * at most 32768 samples), their runs share ONE launch (xe_correlate_batch)
+ * on the service's own CUDA stream, up to 8 streams per launch; each
+ * stream's integrations still come out in order and unchanged.  The flag
+ * XE_SERVICE_NO_BATCH keeps every launch to one stream.
  * Integration k covers sequence numbers [k G, (k+1) G), G = integrate_gulps;
  * it is emitted when its last gulp has been correlated, when a later gulp is
  * committed, or on flush, into one of two pinned output buffers per stream
@@ -314,6 +341,7 @@ typedef struct xe_service *xe_service_t;
 
 #define XE_SERVICE_DRYRUN 1  /* host bookkeeping only: no CUDA call, visibilities are zeros */
 #define XE_SERVICE_MANUAL 2  /* with DRYRUN: work stays in flight until xe_service_dryrun_complete */
+#define XE_SERVICE_NO_BATCH 4 /* every launch serves one stream (no cross-stream launches) */
 
 #define XE_FAULT_LAUNCH 1    /* the stream's next launch fails as a failing CUDA call would */
 #define XE_FAULT_DROP_GULP 2 /* the next committed gulp is lost in transit */
@@ -346,6 +374,7 @@ typedef struct {
   long long device_bytes, host_bytes;
   int state;            /* XE_OK, or the error that stopped the stream */
   int pending, inflight;
+  long long shared_launches;   /* launches this stream shared with other streams */
 } xe_stream_stats;
 
 XE_API xe_status xe_service_create(xe_service_t *out, long long mem_cap_bytes, int flags);
@@ -364,7 +393,7 @@ XE_API xe_status xe_service_poll(xe_service_t svc, int stream, int timeout_ms, x
 XE_API xe_status xe_service_release(xe_service_t svc, int stream, long long index);
 XE_API xe_status xe_service_stats(xe_service_t svc, int stream, xe_stream_stats *out);
 XE_API xe_status xe_service_inject(xe_service_t svc, int stream, int fault);   /* host-side fault injection */
-XE_API xe_status xe_service_dryrun_complete(xe_service_t svc, int stream);
+XE_API xe_status xe_service_dryrun_complete(xe_service_t svc, int stream);   /* -1: every stream */
 XE_API const char *xe_service_last_error(xe_service_t svc);
 
 /* Bounded device-side wait (failure detection): one thread waits until

@@ -319,6 +319,61 @@ xe_status xe_correlate(xe_plan_t p, const uint8_t* d_gulp, int ntime, int accumu
   return XE_OK;
 }
 
+xe_status xe_correlate_batch(int n, const xe_plan_t* plans, const uint8_t* const* d_gulps, const int* ntime,
+                             const int* accumulate, void* stream) {
+  if (n < 1 || n > xe::kMaxBatch || !plans || !d_gulps || !ntime || !accumulate) return XE_ERR_INVALID_ARG;
+  int dev = -1;
+  if (cudaGetDevice(&dev) != cudaSuccess) return XE_ERR_CUDA;
+  for (int k = 0; k < n; ++k) {
+    xe_plan* p = plans[k];
+    if (!p || p->op != XE_OPERAND_FP8_E4M3 || p->device != dev) return XE_ERR_INVALID_ARG;
+    for (int q = 0; q < k; ++q)
+      if (plans[q] == p) return XE_ERR_INVALID_ARG;   // one plan, one accumulator: once per batch
+    xe_status st = check_correlate(p, d_gulps[k], ntime[k], accumulate[k]);
+    if (st != XE_OK) return st;
+    if (ntime[k] > kTcMaxLaunchNtime) return XE_ERR_SHAPE;   // one launch per problem
+    if (ntime[k] > 0 && !aligned16(d_gulps[k])) return XE_ERR_ALIGNMENT;
+  }
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  xe::BatchProblem probs[xe::kMaxBatch];
+  int m = 0, max_ctas = 0;
+  for (int k = 0; k < n; ++k) {
+    xe_plan* p = plans[k];
+    if (ntime[k] == 0) {   // nothing to correlate: as xe_correlate does
+      xe_status st = enqueue_correlate(p, d_gulps[k], 0, accumulate[k], s, p->d_acc);
+      if (st != XE_OK) return st;
+      continue;
+    }
+    xe::BatchProblem& b = probs[m++];
+    xe_status st = encode_gulp_map(p, d_gulps[k], ntime[k], 128, 128, 128, &b.ti);
+    if (st == XE_OK) st = encode_gulp_map(p, d_gulps[k], ntime[k], 64, 128, 64, &b.tj);
+    if (st != XE_OK) return st;
+    b.prm.N = p->N;
+    b.prm.C = p->C;
+    b.prm.nt = (p->N + 127) / 128;
+    b.prm.units = 0;
+    b.prm.nks = (ntime[k] + 127) / 128 * 4;   // whole stages of four 32-sample steps
+    b.prm.accumulate = accumulate[k];
+    b.prm.acc = p->d_acc;
+    b.prm.err = p->d_err;
+    b.prm.timeout_ns = kWaitTimeoutNs;
+    b.prm.split_ws = nullptr;
+    b.prm.split_parts = 0;
+    max_ctas = p->num_sms;
+  }
+  if (m > 0) {
+    int kernels = 0;
+    cudaError_t e = xe::launch_xcorr_batch(probs, m, max_ctas, s, &kernels);
+    if (e != cudaSuccess) return cuda_fail(plans[0], e, "batched tcgen05 launch");
+  }
+  for (int k = 0; k < n; ++k) {
+    xe_plan* p = plans[k];
+    p->samples = (accumulate[k] ? p->samples : 0) + ntime[k];
+    if (ntime[k] > 0) ++p->launches;
+  }
+  return XE_OK;
+}
+
 xe_status xe_correlate_emit(xe_plan_t p, const uint8_t* d_gulp, int ntime, void* d_vis, void* stream) {
   if (!p || !d_vis) return XE_ERR_INVALID_ARG;
   if (p->out_type != XE_OUT_CI32) return XE_ERR_INVALID_ARG;

@@ -48,6 +48,20 @@ int tc8_smem_bytes(int eb);
 cudaError_t launch_xcorr_pair(int eb, const CUtensorMap* tmap_i, const CUtensorMap* tmap_j, const TcParams& prm,
                               int max_ctas, cudaStream_t stream, int* kernels);
 
+// Several independent problems (e.g. the gulps of several streams) in ONE
+// launch of the e4m3 pair kernel: the grid runs the concatenation of their
+// pair units.  Each problem has its own maps (as for launch_xcorr_pair), N,
+// C, nks (one launch: T <= 32768), accumulate flag, accumulator and error
+// word; split_ws must be nullptr (leftover units run whole).  At most
+// kMaxBatch problems; *kernels = 1 on success.
+constexpr int kMaxBatch = 8;
+struct BatchProblem {
+  CUtensorMap ti, tj;
+  TcParams prm;
+};
+cudaError_t launch_xcorr_batch(const BatchProblem* probs, int n, int max_ctas, cudaStream_t stream,
+                               int* kernels);
+
 // Plain CUDA-core correlator (int8 dot products into int32), the baseline.
 cudaError_t launch_xcorr_cudacore(const uint8_t* gulp, int T, int C, int N, int32_t* acc,
                                   int accumulate, int* err, cudaStream_t stream);

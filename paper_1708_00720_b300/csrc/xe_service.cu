@@ -77,6 +77,13 @@ struct Batch {
   std::atomic<int> complete{0};
 };
 
+// Gulps of one stream ready to go in one launch (see next_run).
+struct Run {
+  int first = 0, n = 0;   // ring slots [first, first + n)
+  long long integ = 0;    // integration they belong to
+  bool accumulate = false;
+};
+
 struct Emit {
   long long index = 0, first_seq = 0;
   int gulps = 0, skipped = 0;
@@ -127,6 +134,8 @@ struct StreamImpl {
   // faults
   int fault = 0;
   int state = XE_OK;
+  // cross-stream launches
+  cudaEvent_t comp_mark = nullptr;   // recorded on s_comp before a shared launch
   // stats
   xe_stream_stats st{};
 };
@@ -134,6 +143,8 @@ struct StreamImpl {
 struct ServiceImpl {
   long long cap = 0, used = 0;
   int flags = 0;
+  bool batch = true;     // ready gulps of several e4m3 streams share one launch
+  cudaStream_t s_batch = nullptr;   // the shared launches
   int num_sms = 148;   // of the service's device; a dry run models a 148-SM B300
   bool dry = false, manual = false;
   std::mutex mu;
@@ -152,10 +163,21 @@ struct HostCbEmit {
   Emit* e;
   ServiceImpl* svc;
 };
+struct HostCbShared {
+  std::vector<Batch*> b;
+  ServiceImpl* svc;
+};
 
 void CUDART_CB on_batch_done(void* p) {
   auto* h = static_cast<HostCbBatch*>(p);
   h->b->complete.store(1, std::memory_order_release);
+  h->svc->cv.notify_all();
+  delete h;
+}
+
+void CUDART_CB on_shared_done(void* p) {
+  auto* h = static_cast<HostCbShared*>(p);
+  for (Batch* b : h->b) b->complete.store(1, std::memory_order_release);
   h->svc->cv.notify_all();
   delete h;
 }
@@ -247,24 +269,53 @@ bool try_emit(StreamImpl* s) {
   return true;
 }
 
-// Launch the correlation of the longest run of pending gulps that are
-// contiguous in the ring and belong to the current integration.
-void dispatch(StreamImpl* s) {
+// The longest run of pending gulps that are contiguous in the ring and
+// belong to the current integration, if the stream may launch now.
+bool next_run(StreamImpl* s, Run* r) {
   if (s->state != XE_OK || s->pending.empty() || static_cast<int>(s->inflight.size()) >= kMaxInflight ||
       s->emit_pending)
-    return;
-  const int R = s->cfg.ring_gulps, G = s->cfg.integrate_gulps;
+    return false;
+  const int G = s->cfg.integrate_gulps;
   const long long integ = s->pending.front().seq / G;
-  if (s->integ_index >= 0 && integ != s->integ_index) return;   // previous integration not emitted yet
+  if (s->integ_index >= 0 && integ != s->integ_index) return false;   // previous integration not emitted yet
   int n = 1;
   while (n < static_cast<int>(s->pending.size()) && s->pending[n].seq / G == integ &&
          s->pending[n].slot == s->pending[n - 1].slot + 1)   // contiguous, no wrap
     ++n;
-  const int first = s->pending.front().slot;
+  r->first = s->pending.front().slot;
+  r->n = n;
+  r->integ = integ;
+  r->accumulate = s->integ_has_data;
+  return true;
+}
+
+// Bookkeeping of a run that has been launched (alone or shared).
+void commit_run(StreamImpl* s, const Run& r, std::unique_ptr<Batch> b, bool shared) {
+  for (int k = 0; k < r.n; ++k) {
+    const Gulp& gp = s->pending.front();
+    s->slot_state[gp.slot] = kDispatched;
+    s->integ_t_last = gp.t_commit;
+    if (gp.h2d_done) cudaEventDestroy(gp.h2d_done);
+    s->pending.pop_front();
+  }
+  s->integ_index = r.integ;
+  s->integ_gulps += r.n;
+  s->integ_samples += static_cast<long long>(r.n) * s->cfg.gulp_ntime;
+  s->integ_has_data = true;
+  s->st.launches++;
+  if (shared) s->st.shared_launches++;
+  s->st.gulps_correlated += r.n;
+  if (r.n > s->st.max_batch) s->st.max_batch = r.n;
+  s->inflight.push_back(std::move(b));
+}
+
+// Launch the correlation of the stream's next run on its own.
+void dispatch(StreamImpl* s) {
+  Run r;
+  if (!next_run(s, &r)) return;
   auto b = std::make_unique<Batch>();
-  b->first_slot = first;
-  b->n = n;
-  const bool accumulate = s->integ_has_data;
+  b->first_slot = r.first;
+  b->n = r.n;
   if (s->fault == XE_FAULT_LAUNCH) {
     s->fault = 0;
     fail_stream(s, XE_ERR_CUDA, "injected launch failure");
@@ -273,9 +324,9 @@ void dispatch(StreamImpl* s) {
   if (s->svc->dry) {
     if (!s->svc->manual) b->complete.store(1);
   } else {
-    cudaStreamWaitEvent(s->s_comp, s->pending[n - 1].h2d_done, 0);   // H2D copies are in order
-    const xe_status st = xe_correlate(s->plan, s->d_ring + static_cast<size_t>(first) * s->gulp_bytes,
-                                      n * s->cfg.gulp_ntime, accumulate ? 1 : 0, s->s_comp);
+    cudaStreamWaitEvent(s->s_comp, s->pending[r.n - 1].h2d_done, 0);   // H2D copies are in order
+    const xe_status st = xe_correlate(s->plan, s->d_ring + static_cast<size_t>(r.first) * s->gulp_bytes,
+                                      r.n * s->cfg.gulp_ntime, r.accumulate ? 1 : 0, s->s_comp);
     if (st != XE_OK) {
       fail_stream(s, st, xe_plan_last_error(s->plan));
       return;
@@ -287,22 +338,77 @@ void dispatch(StreamImpl* s) {
       return;
     }
   }
-  for (int k = 0; k < n; ++k) {
-    const Gulp& gp = s->pending.front();
-    s->slot_state[gp.slot] = kDispatched;
-    s->integ_t_last = gp.t_commit;
-    if (gp.h2d_done) cudaEventDestroy(gp.h2d_done);
-    s->pending.pop_front();
+  commit_run(s, r, std::move(b), false);
+}
+
+// Cross-stream batching: when two or more e4m3 streams have runs ready at the
+// same time (each within one launch, at most kMaxBatch streams), they go in
+// ONE launch (xe_correlate_batch) on the service's own CUDA stream, ordered
+// after each stream's earlier compute work and its H2D copies; each stream's
+// later work (integrate, emit) waits for the shared launch.  Streams with an
+// injected fault, other operands or longer runs take the single path.
+void dispatch_shared(ServiceImpl* svc) {
+  StreamImpl* who[xe::kMaxBatch];
+  Run runs[xe::kMaxBatch];
+  int m = 0;
+  for (auto& sp : svc->streams) {
+    StreamImpl* s = sp.get();
+    if (m == xe::kMaxBatch) break;
+    retire(s);
+    if (s->cfg.operand != XE_OPERAND_FP8_E4M3 || s->fault != 0) continue;
+    Run r;
+    if (!next_run(s, &r)) continue;
+    if (static_cast<long long>(r.n) * s->cfg.gulp_ntime > 32768) continue;   // one launch per problem
+    who[m] = s;
+    runs[m] = r;
+    ++m;
   }
-  s->integ_index = integ;
-  s->integ_gulps += n;
-  s->integ_samples += static_cast<long long>(n) * s->cfg.gulp_ntime;
-  s->integ_has_data = true;
-  s->st.launches++;
-  s->st.gulps_correlated += n;
-  if (n > s->st.max_batch) s->st.max_batch = n;
-  s->inflight.push_back(std::move(b));
-  (void)R;
+  if (m < 2) return;
+  std::unique_ptr<Batch> bs[xe::kMaxBatch];
+  for (int k = 0; k < m; ++k) {
+    bs[k] = std::make_unique<Batch>();
+    bs[k]->first_slot = runs[k].first;
+    bs[k]->n = runs[k].n;
+  }
+  if (svc->dry) {
+    if (!svc->manual)
+      for (int k = 0; k < m; ++k) bs[k]->complete.store(1);
+  } else {
+    xe_plan_t plans[xe::kMaxBatch];
+    const uint8_t* gulps[xe::kMaxBatch];
+    int nt[xe::kMaxBatch], acc[xe::kMaxBatch];
+    for (int k = 0; k < m; ++k) {
+      StreamImpl* s = who[k];
+      cudaEventRecord(s->comp_mark, s->s_comp);                  // earlier correlate / integrate work
+      cudaStreamWaitEvent(svc->s_batch, s->comp_mark, 0);
+      cudaStreamWaitEvent(svc->s_batch, s->pending[runs[k].n - 1].h2d_done, 0);
+      plans[k] = s->plan;
+      gulps[k] = s->d_ring + static_cast<size_t>(runs[k].first) * s->gulp_bytes;
+      nt[k] = runs[k].n * s->cfg.gulp_ntime;
+      acc[k] = runs[k].accumulate ? 1 : 0;
+    }
+    const xe_status st = xe_correlate_batch(m, plans, gulps, nt, acc, svc->s_batch);
+    if (st != XE_OK) {
+      // nothing was launched: leave the runs to the single path, which
+      // reports a failing launch per stream
+      return;
+    }
+    cudaEvent_t done;
+    cudaEventCreateWithFlags(&done, cudaEventDisableTiming);
+    cudaEventRecord(done, svc->s_batch);
+    auto* cb = new HostCbShared{{}, svc};
+    for (int k = 0; k < m; ++k) {
+      cudaStreamWaitEvent(who[k]->s_comp, done, 0);
+      cb->b.push_back(bs[k].get());
+    }
+    cudaEventDestroy(done);
+    if (cudaLaunchHostFunc(svc->s_batch, on_shared_done, cb) != cudaSuccess) {
+      delete cb;
+      for (int k = 0; k < m; ++k) fail_stream(who[k], XE_ERR_CUDA, "cudaLaunchHostFunc failed");
+      return;
+    }
+  }
+  for (int k = 0; k < m; ++k) commit_run(who[k], runs[k], std::move(bs[k]), true);
 }
 
 // The integration is complete when its last gulp has been dispatched, or on
@@ -342,6 +448,14 @@ void pump_stream(StreamImpl* s) {
 }
 
 void pump_all(ServiceImpl* svc) {
+  // close and emit finished integrations first, so that their streams can
+  // take part in a shared launch of the next gulps
+  for (auto& s : svc->streams) {
+    retire(s.get());
+    maybe_close(s.get());
+    if (s->emit_pending) try_emit(s.get());
+  }
+  if (svc->batch) dispatch_shared(svc);
   for (auto& s : svc->streams) pump_stream(s.get());
 }
 
@@ -372,6 +486,7 @@ void free_stream_resources(StreamImpl* s, bool dry) {
   for (auto& b : s->inflight)
     if (b->done) cudaEventDestroy(b->done);
   if (s->d2h_done) cudaEventDestroy(s->d2h_done);
+  if (s->comp_mark) cudaEventDestroy(s->comp_mark);
   if (s->plan) xe_plan_destroy(s->plan);
   cudaFreeHost(s->h_ring);
   for (auto& p : s->h_out) cudaFreeHost(p);
@@ -423,7 +538,7 @@ XE_API xe_status xe_wait_flag(const int* d_flag, int expected, long long timeout
 XE_API xe_status xe_service_create(xe_service_t* out, long long mem_cap_bytes, int flags) {
   if (!out) return XE_ERR_INVALID_ARG;
   *out = nullptr;
-  if (flags & ~(XE_SERVICE_DRYRUN | XE_SERVICE_MANUAL)) return XE_ERR_INVALID_ARG;
+  if (flags & ~(XE_SERVICE_DRYRUN | XE_SERVICE_MANUAL | XE_SERVICE_NO_BATCH)) return XE_ERR_INVALID_ARG;
   if ((flags & XE_SERVICE_MANUAL) && !(flags & XE_SERVICE_DRYRUN)) return XE_ERR_INVALID_ARG;
   const bool dry = flags & XE_SERVICE_DRYRUN;
   long long cap = mem_cap_bytes;
@@ -450,6 +565,12 @@ XE_API xe_status xe_service_create(xe_service_t* out, long long mem_cap_bytes, i
   ServiceImpl& S = svc->impl;
   S.cap = cap;
   S.num_sms = sms;
+  S.batch = !(flags & XE_SERVICE_NO_BATCH);
+  if (!dry && cudaStreamCreateWithFlags(&S.s_batch, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    delete svc;
+    return XE_ERR_CUDA;
+  }
   S.flags = flags;
   S.dry = dry;
   S.manual = flags & XE_SERVICE_MANUAL;
@@ -467,7 +588,9 @@ XE_API xe_status xe_service_destroy(xe_service_t svc) {
   }
   S.cv.notify_all();
   if (S.worker.joinable()) S.worker.join();
+  if (S.s_batch) cudaStreamSynchronize(S.s_batch);   // shared launches read every stream's ring
   for (auto& s : S.streams) free_stream_resources(s.get(), S.dry);
+  if (S.s_batch) cudaStreamDestroy(S.s_batch);
   delete svc;
   return XE_OK;
 }
@@ -524,6 +647,7 @@ XE_API xe_status xe_service_add_stream(xe_service_t svc, const xe_stream_config*
     ok = ok && cudaStreamCreateWithFlags(&s->s_comp, cudaStreamNonBlocking) == cudaSuccess;
     ok = ok && cudaStreamCreateWithFlags(&s->s_d2h, cudaStreamNonBlocking) == cudaSuccess;
     ok = ok && cudaEventCreateWithFlags(&s->d2h_done, cudaEventDisableTiming) == cudaSuccess;
+    ok = ok && cudaEventCreateWithFlags(&s->comp_mark, cudaEventDisableTiming) == cudaSuccess;
     if (ok) ok = cudaEventRecord(s->d2h_done, s->s_d2h) == cudaSuccess;
     if (!ok) {
       cudaGetLastError();
@@ -614,7 +738,7 @@ XE_API xe_status xe_service_commit(xe_service_t svc, int id, long long seq) {
   s->last_seq = seq;
   s->st.committed++;
   s->pending.push_back(g);
-  pump_stream(s);
+  pump_all(&S);   // other streams' ready gulps may share this launch
   S.cv.notify_all();
   return XE_OK;
 }
@@ -721,14 +845,22 @@ XE_API xe_status xe_service_dryrun_complete(xe_service_t svc, int id) {
   ServiceImpl& S = svc->impl;
   if (!S.manual) return XE_ERR_INVALID_ARG;
   std::lock_guard<std::mutex> lk(S.mu);
+  auto complete = [](StreamImpl* s) {
+    for (auto& b : s->inflight) b->complete.store(1);
+    for (auto& e : s->emits)
+      if (!e->ready.load()) {
+        e->t_done = now_ms();
+        e->ready.store(1);
+      }
+  };
+  if (id == -1) {   // every stream at once: their next runs may then share a launch
+    for (auto& s : S.streams) complete(s.get());
+    pump_all(&S);
+    return XE_OK;
+  }
   StreamImpl* s = get_stream(&S, id);
   if (!s) return XE_ERR_INVALID_ARG;
-  for (auto& b : s->inflight) b->complete.store(1);
-  for (auto& e : s->emits)
-    if (!e->ready.load()) {
-      e->t_done = now_ms();
-      e->ready.store(1);
-    }
+  complete(s);
   pump_stream(s);
   return XE_OK;
 }

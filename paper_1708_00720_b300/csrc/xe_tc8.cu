@@ -379,13 +379,47 @@ constexpr int kMinPartSamples = 1024;        // shortest part worth its own epil
 constexpr int kSplitTile = kTile * kTile;    // int2 per CTA and workspace slot
 
 struct Item {
-  int u;        // pair unit
+  int p;        // problem of the launch
+  int u;        // pair unit of that problem
   int k0, k1;   // its 32-sample steps [k0, k1)
   int lo;       // leftover unit index of a part, else -1
 };
 
+// One launch: the problems it correlates (one for a plan's call, up to
+// kMaxBatch for a batched call), their maps and the concatenation of their
+// pair units (problem k owns global units [prefix[k], prefix[k + 1])).
+// Passed as a __grid_constant__ parameter, so the tensor maps stay in
+// parameter space as TMA requires of a map it is given by address.
+struct ProbDev {
+  int32_t* acc;          // [C][N (N + 1) / 2][2]
+  int* err;              // device error word of the problem's plan
+  long long acc_pairs;   // int2 elements of acc (debug index checks)
+  int N, nt, per_chan, nks, accumulate;
+};
+struct PairLaunch {
+  CUtensorMap ti[kMaxBatch];   // I tiles: box {128, 1, rows}, 128-byte swizzle
+  CUtensorMap tj[kMaxBatch];   // half J tiles: box {64, 1, rows}, 64-byte swizzle
+  ProbDev p[kMaxBatch];
+  int prefix[kMaxBatch + 1];
+  int nprob, units, split_parts;
+  int2* split_ws;              // time-sliced leftover units (one problem only), or nullptr
+  long long ws_pairs;
+  unsigned long long timeout_ns;
+};
+static_assert(sizeof(PairLaunch) <= 4096, "kernel parameter space");
+static_assert(alignof(CUtensorMap) >= 64, "tensor maps in parameter space need 64-byte alignment");
+
+// A wait gave up: stop every role of this CTA and record the code in every
+// problem's error word (the launch's results are all in doubt).
+__device__ __forceinline__ void fail_all(const Smem& s, const PairLaunch& L, int code) {
+  atomicExch(s.abort_flag, 1);
+  for (int k = 0; k < L.nprob; ++k) atomicOr(L.p[k].err, code);
+}
+
 // Schedule of this cluster in shared memory: {items, R, cl, ncl, nks} and
-// then the item after the R full rounds, if any, as {u, k0, k1, lo}.
+// then the item after the R full rounds, if any, as {u, k0, k1, lo} (u a
+// global unit; k1 = -1: the whole unit).  nks and the parts belong to a
+// single-problem launch; a batched launch has no parts.
 constexpr int kSchedInts = 5 + 4;
 static_assert((2 + kSchedInts) * 4 <= kCtlBytes, "control words after the barriers");
 __device__ inline void fill_sched(int* sc, int units, int cl, int ncl, int nks, int steps, int q) {
@@ -393,7 +427,7 @@ __device__ inline void fill_sched(int* sc, int units, int cl, int ncl, int nks, 
   int n = 0;
   int* t = sc + 5;
   if (q == 0 && cl < L) {
-    t[0] = R * ncl + cl; t[1] = 0; t[2] = nks; t[3] = -1;
+    t[0] = R * ncl + cl; t[1] = 0; t[2] = -1; t[3] = -1;
     n = 1;
   } else if (q > 0 && cl < q * L) {
     const int l = cl / q, i = cl - l * q;
@@ -408,21 +442,27 @@ __device__ inline void fill_sched(int* sc, int units, int cl, int ncl, int nks, 
 }
 
 // Item i of this cluster (the schedule is read from shared memory each time:
-// registers are scarce in every warp role).
-__device__ __forceinline__ Item item_at(const int* sc, int i) {
+// registers are scarce in every warp role), with its problem.
+__device__ __forceinline__ Item item_at(const int* sc, int i, const PairLaunch& L) {
   Item w;
   const int R = sc[1];
+  int g;
   if (i < R) {
-    w.u = sc[2] + i * sc[3];
+    g = sc[2] + i * sc[3];
     w.k0 = 0;
-    w.k1 = sc[4];
+    w.k1 = -1;
     w.lo = -1;
   } else {
-    w.u = sc[5];
+    g = sc[5];
     w.k0 = sc[6];
     w.k1 = sc[7];
     w.lo = sc[8];
   }
+  int p = 0;
+  while (p + 1 < L.nprob && g >= L.prefix[p + 1]) ++p;
+  w.p = p;
+  w.u = g - L.prefix[p];
+  if (w.k1 < 0) w.k1 = L.p[p].nks;
   return w;
 }
 
@@ -656,7 +696,7 @@ __device__ __forceinline__ int2 unbias(int2 raw, float rre, float rim, float cre
 
 template <int EB>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
-xcorr_tc8_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant__ CUtensorMap tmap_j, TcParams prm) {
+xcorr_tc8_kernel(const __grid_constant__ PairLaunch L) {
   using G = Geo<EB>;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
@@ -666,10 +706,7 @@ xcorr_tc8_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant
   const uint32_t rank = cluster_rank();
   const uint32_t peer = rank ^ 1u;
   const int cl = blockIdx.x >> 1, ncl = gridDim.x >> 1;
-  const int nt = prm.nt;
-  const int per_chan = pairs_per_channel(nt);
-  const int nks = prm.nks;
-  const uint64_t lim = prm.timeout_ns;
+  const uint64_t lim = L.timeout_ns;
   volatile int* abort_flag = s.abort_flag;
 
   if (tid == 0) {
@@ -691,10 +728,12 @@ xcorr_tc8_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant
     }
     mbar_init(s.final_bar, 1);
     *s.abort_flag = 0;
-    fill_sched(s.sched, prm.units, cl, ncl, nks, G::kSteps, prm.split_parts);
+    fill_sched(s.sched, L.units, cl, ncl, L.p[0].nks, G::kSteps, L.split_parts);
     mbar_fence_init();
-    tma_prefetch_desc(&tmap);
-    tma_prefetch_desc(&tmap_j);
+    for (int k = 0; k < L.nprob; ++k) {
+      tma_prefetch_desc(&L.ti[k]);
+      tma_prefetch_desc(&L.tj[k]);
+    }
   }
   // partial-sum blocks a kernel never writes (the float16 B side keeps its
   // sums in the first block) must read as zero
@@ -718,13 +757,13 @@ xcorr_tc8_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant
       int rit = 0;                              // raw stage counter (4 steps each)
       bool ok = true;
       for (int it = 0; it < s.sched[0] && ok; ++it) {
-        const Item w = item_at(s.sched, it);
-        const Unit t = decode_unit(w.u, per_chan, nt, rank);
+        const Item w = item_at(s.sched, it, L);
+        const Unit t = decode_unit(w.u, L.p[w.p].per_chan, L.p[w.p].nt, rank);
         const bool own_diag = (t.ti == t.tj);
         for (int ks = w.k0; ks < w.k1; ks += G::kSteps, ++rit) {
           const int st = rit % kRawStages;
           if (!wait_or_abort(&s.raw_empty[st], ((rit / kRawStages) & 1) ^ 1, lim, abort_flag)) {
-            fail(s, prm.err, kErrWaitRawEmpty);
+            fail_all(s, L, kErrWaitRawEmpty);
             ok = false;
             break;
           }
@@ -732,13 +771,14 @@ xcorr_tc8_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant
           const int kp = ks + kPrefetch * G::kSteps;   // the stage to prefetch into L2
           if (tile == 0) {
             mbar_arrive_expect_tx(&s.raw_full[st], G::kRawTile);
-            tma_load_3d(dst, &tmap, &s.raw_full[st], t.ti * kTile, t.c, ks * kStep);
-            if (kp < w.k1) tma_prefetch_3d(&tmap, t.ti * kTile, t.c, kp * kStep);
+            tma_load_3d(dst, &L.ti[w.p], &s.raw_full[st], t.ti * kTile, t.c, ks * kStep);
+            if (kp < w.k1) tma_prefetch_3d(&L.ti[w.p], t.ti * kTile, t.c, kp * kStep);
           } else if (!own_diag) {
             mbar_arrive_expect_tx(&s.raw_full[st], G::kRawHalf);
-            tma_load_3d(dst, &tmap_j, &s.raw_full[st], t.tj * kTile + kHalf * static_cast<int>(rank), t.c,
+            tma_load_3d(dst, &L.tj[w.p], &s.raw_full[st], t.tj * kTile + kHalf * static_cast<int>(rank), t.c,
                         ks * kStep);
-            if (kp < w.k1) tma_prefetch_3d(&tmap_j, t.tj * kTile + kHalf * static_cast<int>(rank), t.c, kp * kStep);
+            if (kp < w.k1)
+              tma_prefetch_3d(&L.tj[w.p], t.tj * kTile + kHalf * static_cast<int>(rank), t.c, kp * kStep);
           } else {
             mbar_arrive(&s.raw_full[st]);    // the I tile serves as J
           }
@@ -760,12 +800,12 @@ xcorr_tc8_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant
       int sit = 0;
       bool ok = true;
       for (int it = 0; it < s.sched[0] && ok; ++it) {
-        const Item w = item_at(s.sched, it);
+        const Item w = item_at(s.sched, it, L);
         for (int ks = w.k0; ks < w.k1; ks += G::kSteps, ++sit) {
           if ((sit & 1) != fwd) continue;
           const int st = sit % kOpStages;
           if (!wait_or_abort(&s.op_full[st], (sit / kOpStages) & 1, lim, abort_flag)) {
-            fail(s, prm.err, kErrWaitOpFull);
+            fail_all(s, L, kErrWaitOpFull);
             ok = false;
             break;
           }
@@ -787,7 +827,7 @@ xcorr_tc8_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant
       const uint64_t desc0 = EB == 1 ? sdesc_mn_sw64(smem_u32(s.op)) : sdesc_k_sw128(smem_u32(s.op));
       const uint32_t d_re = tmem, d_im = tmem + 128;
       for (int it = 0; it < s.sched[0] && ok; ++it, ++ui) {
-        const Item w = item_at(s.sched, it);
+        const Item w = item_at(s.sched, it, L);
         const uint32_t free_par = (ui & 1) ^ 1;
         // D is released in two halves.  Once the epilogue has read D_re, the
         // real-part MMAs of the operand stages already resident (up to the
@@ -796,7 +836,7 @@ xcorr_tc8_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant
         const int nst = (w.k1 - w.k0 + G::kSteps - 1) / G::kSteps;
         const int head = nst < kOpStages ? nst : kOpStages;
         if (!wait_or_abort(s.acc_empty, free_par, lim, abort_flag)) {
-          fail(s, prm.err, kErrWaitAccEmpty);
+          fail_all(s, L, kErrWaitAccEmpty);
           break;
         }
         tc_fence_after();
@@ -805,7 +845,7 @@ xcorr_tc8_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant
           uint32_t phh = ph;
           for (int p = 0; p < head; ++p) {
             if (!wait_or_abort(&s.op_full[sh], phh, lim, abort_flag)) {
-              fail(s, prm.err, kErrWaitOpFull);
+              fail_all(s, L, kErrWaitOpFull);
               ok = false;
               break;
             }
@@ -820,7 +860,7 @@ xcorr_tc8_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant
         }
         if (!ok) break;
         if (!wait_or_abort(s.acc_empty_im, free_par, lim, abort_flag)) {
-          fail(s, prm.err, kErrWaitAccEmpty);
+          fail_all(s, L, kErrWaitAccEmpty);
           break;
         }
         tc_fence_after();
@@ -835,7 +875,7 @@ xcorr_tc8_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant
         }
         for (int ks = w.k0 + head * G::kSteps; ks < w.k1; ks += G::kSteps) {
           if (!wait_or_abort(&s.op_full[st], ph, lim, abort_flag)) {
-            fail(s, prm.err, kErrWaitOpFull);
+            fail_all(s, L, kErrWaitOpFull);
             ok = false;
             break;
           }
@@ -863,14 +903,14 @@ xcorr_tc8_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant
     int sit = 0, ui = 0;
     bool ok = true;
     for (int it = 0; it < s.sched[0] && ok; ++it, ++ui) {
-      const Item w = item_at(s.sched, it);
+      const Item w = item_at(s.sched, it, L);
       PairSums ps;
       ps.zero();
       int since_fold = 0;
       for (int ks = w.k0; ks < w.k1; ks += G::kSteps, ++sit) {
         const int rst = sit % kRawStages, ost = sit % kOpStages;
         if (!wait_or_abort(&s.raw_full[rst], (sit / kRawStages) & 1, lim, abort_flag)) {
-          fail(s, prm.err, kErrWaitRawFull);
+          fail_all(s, L, kErrWaitRawFull);
           ok = false;
           break;
         }
@@ -886,7 +926,7 @@ xcorr_tc8_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant
         // stages leave little slack)
         release_raw_after_loads<4 * G::kSteps>(&dv[0][0], &s.raw_empty[rst], lane);
         if (!wait_or_abort(&s.op_empty[ost], ((sit / kOpStages) & 1) ^ 1, lim, abort_flag)) {
-          fail(s, prm.err, kErrWaitOpEmpty);
+          fail_all(s, L, kErrWaitOpEmpty);
           ok = false;
           break;
         }
@@ -919,7 +959,7 @@ xcorr_tc8_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant
       ps.reduce();
       const int slot = ui & 1;
       if (!wait_or_abort(&s.sums_empty[slot], ((ui >> 1) & 1) ^ 1, lim, abort_flag)) {
-        fail(s, prm.err, kErrWaitSumsEmpty);
+        fail_all(s, L, kErrWaitSumsEmpty);
         break;
       }
       int* sl = s.sums + slot * kSlotInts;
@@ -956,8 +996,8 @@ xcorr_tc8_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant
     int sit = 0, ui = 0;
     bool ok = true;
     for (int it = 0; it < s.sched[0] && ok; ++it, ++ui) {
-      const Item w = item_at(s.sched, it);
-      const Unit t = decode_unit(w.u, per_chan, nt, rank);
+      const Item w = item_at(s.sched, it, L);
+      const Unit t = decode_unit(w.u, L.p[w.p].per_chan, L.p[w.p].nt, rank);
       const bool own_diag = (t.ti == t.tj);
       // sums of the biased parts of the chunk's 16 inputs: byte lanes (at most
       // 4 x 4 x 15 = 240 between folds), then 16-bit lanes ([2k]: bytes 0 and
@@ -968,7 +1008,7 @@ xcorr_tc8_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant
       for (int ks = w.k0; ks < w.k1; ks += G::kSteps, ++sit) {
         const int rst = sit % kRawStages, ost = sit % kOpStages;
         if (!wait_or_abort(&s.raw_full[rst], (sit / kRawStages) & 1, lim, abort_flag)) {
-          fail(s, prm.err, kErrWaitRawFull);
+          fail_all(s, L, kErrWaitRawFull);
           ok = false;
           break;
         }
@@ -980,7 +1020,7 @@ xcorr_tc8_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant
         for (int sub = 0; sub < G::kSteps; ++sub) v[sub] = lds128(src + sub * sstep);
         release_raw_after_loads<4 * G::kSteps>(&v[0].x, &s.raw_empty[rst], lane);
         if (!wait_or_abort(&s.op_empty[ost], ((sit / kOpStages) & 1) ^ 1, lim, abort_flag)) {
-          fail(s, prm.err, kErrWaitOpEmpty);
+          fail_all(s, L, kErrWaitOpEmpty);
           ok = false;
           break;
         }
@@ -1044,7 +1084,7 @@ xcorr_tc8_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant
       }
       const int slot = ui & 1;
       if (!wait_or_abort(&s.sums_empty[slot], ((ui >> 1) & 1) ^ 1, lim, abort_flag)) {
-        fail(s, prm.err, kErrWaitSumsEmpty);
+        fail_all(s, L, kErrWaitSumsEmpty);
         break;
       }
       int* sl = s.sums + slot * kSlotInts + 2 * kTile + g * 2 * kHalf;   // this warp's block
@@ -1071,8 +1111,8 @@ xcorr_tc8_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant
     int sit = 0, ui = 0;
     bool ok = true;
     for (int it = 0; it < s.sched[0] && ok; ++it, ++ui) {
-      const Item w = item_at(s.sched, it);
-      const Unit t = decode_unit(w.u, per_chan, nt, rank);
+      const Item w = item_at(s.sched, it, L);
+      const Unit t = decode_unit(w.u, L.p[w.p].per_chan, L.p[w.p].nt, rank);
       const bool own_diag = (t.ti == t.tj);
       PairSums ps;
       ps.zero();
@@ -1080,7 +1120,7 @@ xcorr_tc8_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant
       for (int ks = w.k0; ks < w.k1; ks += G::kSteps, ++sit) {
         const int rst = sit % kRawStages, ost = sit % kOpStages;
         if (!wait_or_abort(&s.raw_full[rst], (sit / kRawStages) & 1, lim, abort_flag)) {
-          fail(s, prm.err, kErrWaitRawFull);
+          fail_all(s, L, kErrWaitRawFull);
           ok = false;
           break;
         }
@@ -1096,7 +1136,7 @@ xcorr_tc8_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant
           ldsm_x4_trans(rowJ + sub * subJ, dv[sub][0], dv[sub][1], dv[sub][2], dv[sub][3]);
         release_raw_after_loads<4 * G::kSteps>(&dv[0][0], &s.raw_empty[rst], lane);
         if (!wait_or_abort(&s.op_empty[ost], ((sit / kOpStages) & 1) ^ 1, lim, abort_flag)) {
-          fail(s, prm.err, kErrWaitOpEmpty);
+          fail_all(s, L, kErrWaitOpEmpty);
           ok = false;
           break;
         }
@@ -1130,7 +1170,7 @@ xcorr_tc8_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant
       ps.reduce();
       const int slot = ui & 1;
       if (!wait_or_abort(&s.sums_empty[slot], ((ui >> 1) & 1) ^ 1, lim, abort_flag)) {
-        fail(s, prm.err, kErrWaitSumsEmpty);
+        fail_all(s, L, kErrWaitSumsEmpty);
         break;
       }
       int* sl = s.sums + slot * kSlotInts + 2 * kTile;
@@ -1154,32 +1194,33 @@ xcorr_tc8_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant
     // reached equally often by all four warps); after an abort it only
     // skips work.
     const int quad = warp & 3;
-    const int L = 32 * quad + lane;                 // TMEM lane = accumulator row; also a column index
-    const int il = lane_to_input(L);                // input offset of row L in its tile
-    const int jl = col_to_input<EB>(L);             // input offset of column L in its tile
-    const long long nbl = static_cast<long long>(prm.N) * (prm.N + 1) / 2;
+    const int lr = 32 * quad + lane;                 // TMEM lane = accumulator row; also a column index
+    const int il = lane_to_input(lr);                // input offset of row lr in its tile
+    const int jl = col_to_input<EB>(lr);             // input offset of column lr in its tile
     int* const sre = s.stage + quad * 2 * kStageBufs * kStageChunk;   // this warp's staged real parts
     int* const sim = sre + kStageBufs * kStageChunk;                   // and imaginary parts
     bool ok = true;
     int ui = 0;
     for (int it = 0; it < s.sched[0]; ++it, ++ui) {
-      const Item w = item_at(s.sched, it);
-      const Unit t = decode_unit(w.u, per_chan, nt, rank);
+      const Item w = item_at(s.sched, it, L);
+      const ProbDev& P = L.p[w.p];
+      const Unit t = decode_unit(w.u, P.per_chan, P.nt, rank);
+      const long long nbl = static_cast<long long>(P.N) * (P.N + 1) / 2;
       const int T_pad = (w.k1 - w.k0) * kStep;
       const int slot = ui & 1;
       if (ok && !wait_or_abort(&s.sums_full[slot], (ui >> 1) & 1, lim, abort_flag)) {
-        fail(s, prm.err, kErrWaitSumsFull);
+        fail_all(s, L, kErrWaitSumsFull);
         ok = false;
       }
       const int* sl = s.sums + slot * kSlotInts;
       float row_re = 0.f, row_im = 0.f;
       if (ok) {
-        // bias corrections of this lane's row and of column L (see unbias)
+        // bias corrections of this lane's row and of column lr (see unbias)
         row_re = static_cast<float>(-8 * (sl[il] + sl[kTile + il]) + 128 * T_pad);
         row_im = static_cast<float>(8 * (sl[il] - sl[kTile + il]));
-        // column L is J input jl; its half (L / 64) is held by CTA L / 64,
+        // column lr is J input jl; its half (lr / 64) is held by CTA lr / 64,
         // whose B-side warps each left partial sums in a block of their own
-        const uint32_t holder = static_cast<uint32_t>(L >> 6);
+        const uint32_t holder = static_cast<uint32_t>(lr >> 6);
         const int jo = jl - kHalf * static_cast<int>(holder);
         const int* pq = sl + 2 * kTile;
         int pjv = 0, qjv = 0;
@@ -1189,19 +1230,19 @@ xcorr_tc8_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant
           pjv += holder == rank ? blk[jo] : ld_peer(blk + jo, holder);
           qjv += holder == rank ? blk[kHalf + jo] : ld_peer(blk + kHalf + jo, holder);
         }
-        s.colcorr[L] = static_cast<float>(-8 * (pjv + qjv));
-        s.colcorr[kTile + L] = static_cast<float>(-8 * (pjv - qjv));
+        s.colcorr[lr] = static_cast<float>(-8 * (pjv + qjv));
+        s.colcorr[kTile + lr] = static_cast<float>(-8 * (pjv - qjv));
       }
       if (w.lo < 0) {
-        // packed-triangle offsets of row L's and column L's inputs (N <= 8192 fits int)
+        // packed-triangle offsets of row lr's and column lr's inputs (N <= 8192 fits int)
         const int gi = t.ti * kTile + il, gj = t.tj * kTile + jl;
-        s.rowoff[L] = gi < prm.N ? gi * (gi + 1) / 2 : 0;
-        s.coloff[L] = gj < prm.N ? gj * (gj + 1) / 2 : 0;
+        s.rowoff[lr] = gi < P.N ? gi * (gi + 1) / 2 : 0;
+        s.coloff[lr] = gj < P.N ? gj * (gj + 1) / 2 : 0;
       } else {
         // a part: rows of the compact workspace tile, in accumulator-row
         // order (a transposed part's rows are J inputs: row input_to_lane(jl))
-        s.rowoff[L] = L * kTile;
-        s.coloff[L] = input_to_lane(jl) * kTile;
+        s.rowoff[lr] = lr * kTile;
+        s.coloff[lr] = input_to_lane(jl) * kTile;
       }
       asm volatile("bar.sync 1, 128;" ::: "memory");
       if (lane == 0) {   // this slot's own sums and the partner's half of J have been read
@@ -1209,7 +1250,7 @@ xcorr_tc8_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant
         arrive_relaxed_at(&s.sums_empty[slot], peer);
       }
       if (ok && !wait_or_abort(s.acc_full, ui & 1, lim, abort_flag)) {
-        fail(s, prm.err, kErrWaitAccFull);
+        fail_all(s, L, kErrWaitAccFull);
         ok = false;
       }
       ok = __all_sync(0xFFFFFFFFu, ok);
@@ -1247,17 +1288,17 @@ xcorr_tc8_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant
         released = true;
         // a part goes to its workspace slot (stored, never added): the tile's
         // first column input then lands on column 0
-        const int accumulate = w.lo < 0 ? prm.accumulate : 0;
+        const int accumulate = w.lo < 0 ? P.accumulate : 0;
         int2* const acc =
-            w.lo < 0 ? reinterpret_cast<int2*>(prm.acc) + static_cast<long long>(t.c) * nbl
-                     : prm.split_ws + (static_cast<long long>(2 * cl + rank) * kSplitTile -
+            w.lo < 0 ? reinterpret_cast<int2*>(P.acc) + static_cast<long long>(t.c) * nbl
+                     : L.split_ws + (static_cast<long long>(2 * cl + rank) * kSplitTile -
                                        (t.transposed ? t.ti : t.tj) * kTile);
         // the buffer written, for the debug build's index checks
-        const int2* const wbase = w.lo < 0 ? reinterpret_cast<const int2*>(prm.acc) : prm.split_ws;
-        const long long wlen = w.lo < 0 ? prm.acc_pairs : prm.ws_pairs;
+        const int2* const wbase = w.lo < 0 ? reinterpret_cast<const int2*>(P.acc) : L.split_ws;
+        const long long wlen = w.lo < 0 ? P.acc_pairs : L.ws_pairs;
         // a tile strictly below the diagonal and inside N needs no checks
-        const bool full = !t.transposed && t.ti > t.tj && t.ti * kTile + kTile <= prm.N;
-        const bool tfull = t.transposed && t.tj * kTile + kTile <= prm.N;
+        const bool full = !t.transposed && t.ti > t.tj && t.ti * kTile + kTile <= P.N;
+        const bool tfull = t.transposed && t.tj * kTile + kTile <= P.N;
         const int gI = t.ti * kTile + il;           // this lane's row input
         const int* ro = s.rowoff + 32 * quad;
 #pragma unroll 1
@@ -1281,7 +1322,7 @@ xcorr_tc8_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant
               for (int r = 0; r < 32; ++r) {
                 const float rre = __shfl_sync(0xFFFFFFFFu, row_re, r), rim = __shfl_sync(0xFFFFFFFFu, row_im, r);
                 int2* dst = accj + ro[r];
-                if (debug_in_bounds(dst, wbase, wlen, prm.err))
+                if (debug_in_bounds(dst, wbase, wlen, P.err))
                   *dst = unbias<EB>(staged(sb, r, lane), rre, rim, cre, cim);
               }
             } else if (full) {
@@ -1290,7 +1331,7 @@ xcorr_tc8_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant
                 const float rre = __shfl_sync(0xFFFFFFFFu, row_re, r), rim = __shfl_sync(0xFFFFFFFFu, row_im, r);
                 const int2 v = unbias<EB>(staged(sb, r, lane), rre, rim, cre, cim);
                 int2* dst = accj + ro[r];
-                if (debug_in_bounds(dst, wbase, wlen, prm.err)) {
+                if (debug_in_bounds(dst, wbase, wlen, P.err)) {
                   const int2 o = *dst;
                   *dst = make_int2(o.x + v.x, o.y + v.y);
                 }
@@ -1300,10 +1341,10 @@ xcorr_tc8_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant
               for (int r = 0; r < 32; ++r) {
                 const float rre = __shfl_sync(0xFFFFFFFFu, row_re, r), rim = __shfl_sync(0xFFFFFFFFu, row_im, r);
                 const int gi = t.ti * kTile + lane_to_input(32 * quad + r);
-                if (gi < prm.N && gj <= gi) {
+                if (gi < P.N && gj <= gi) {
                   const int2 v = unbias<EB>(staged(sb, r, lane), rre, rim, cre, cim);
                   int2* dst = accj + ro[r];
-                  if (!debug_in_bounds(dst, wbase, wlen, prm.err)) continue;
+                  if (!debug_in_bounds(dst, wbase, wlen, P.err)) continue;
                   if (accumulate) {
                     const int2 o = *dst;
                     *dst = make_int2(o.x + v.x, o.y + v.y);
@@ -1320,11 +1361,11 @@ xcorr_tc8_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant
             int2* acci = acc + gI;
 #pragma unroll 4
             for (int k = 0; k < 32; ++k) {
-              if (tfull || t.tj * kTile + col_to_input<EB>(cc + k) < prm.N) {
+              if (tfull || t.tj * kTile + col_to_input<EB>(cc + k) < P.N) {
                 const int2 v = unbias<EB>(staged(sb, lane, k), row_re, row_im, s.colcorr[cc + k],
                                           s.colcorr[kTile + cc + k]);
                 int2* dst = acci + s.coloff[cc + k];
-                if (!debug_in_bounds(dst, wbase, wlen, prm.err)) continue;
+                if (!debug_in_bounds(dst, wbase, wlen, P.err)) continue;
                 if (accumulate) {
                   const int2 o = *dst;
                   *dst = make_int2(o.x + v.x, o.y - v.y);
@@ -1355,7 +1396,8 @@ xcorr_tc8_kernel(const __grid_constant__ CUtensorMap tmap, const __grid_constant
   // Teardown: every MMA of the pair has completed (both CTAs' tensor memory
   // and shared memory are read by it) before either CTA frees or leaves.
   if (warp == 1 && lane == 0) {
-    if (!mbar_wait(s.final_bar, 0, lim)) atomicOr(prm.err, kErrWaitFinal);
+    if (!mbar_wait(s.final_bar, 0, lim))
+      for (int k = 0; k < L.nprob; ++k) atomicOr(L.p[k].err, kErrWaitFinal);
   }
   tc_fence_before();
   __syncthreads();
@@ -1419,57 +1461,93 @@ __global__ void __launch_bounds__(256) split_combine_kernel(const CombineParams 
 int tc8_smem_bytes(int eb) { return eb == 1 ? tc8::Geo<1>::kSmemBytes : tc8::Geo<2>::kSmemBytes; }
 
 namespace {
+// Clusters (pairs of SMs) of the pair kernel that can be resident at once,
+// asked once per process and operand width.
+template <int EB>
+int resident_clusters() {
+  static int n = -1;
+  if (n < 0) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(2, 1, 1);
+    cfg.blockDim = dim3(tc8::kThreads, 1, 1);
+    cfg.dynamicSmemBytes = tc8::Geo<EB>::kSmemBytes;
+    int r = 0;
+    if (cudaOccupancyMaxActiveClusters(&r, tc8::xcorr_tc8_kernel<EB>, &cfg) != cudaSuccess || r < 1) {
+      cudaGetLastError();
+      r = 0;
+    }
+    n = r;
+  }
+  return n;
+}
+
+// Problem k of a launch description from a plan's parameters.
+void set_problem(tc8::PairLaunch& L, int k, const CUtensorMap& ti, const CUtensorMap& tj, const TcParams& prm) {
+  L.ti[k] = ti;
+  L.tj[k] = tj;
+  tc8::ProbDev& d = L.p[k];
+  d.acc = prm.acc;
+  d.err = prm.err;
+  d.acc_pairs = static_cast<long long>(prm.C) * prm.N * (prm.N + 1) / 2;
+  d.N = prm.N;
+  d.nt = prm.nt;
+  d.per_chan = tc8::pairs_per_channel(prm.nt);
+  d.nks = prm.nks;
+  d.accumulate = prm.accumulate;
+}
+
+template <int EB>
+cudaError_t launch_table(tc8::PairLaunch& L, long long units, int max_ctas, cudaStream_t stream,
+                         long long* clusters_out) {
+  constexpr int smem = tc8::Geo<EB>::kSmemBytes;
+  cudaError_t e = cudaFuncSetAttribute(tc8::xcorr_tc8_kernel<EB>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  if (units > 0x7FFFFFFFLL) return cudaErrorInvalidValue;
+  L.units = static_cast<int>(units);
+  long long clusters = max_ctas / 2;
+  const int res = resident_clusters<EB>();
+  if (res > 0 && res < clusters) clusters = res;
+  if (units < clusters) clusters = units;
+  if (clusters < 1) clusters = 1;
+  *clusters_out = clusters;
+  L.split_parts = L.split_ws ? tc8::split_parts(units, clusters, L.p[0].nks, tc8::Geo<EB>::kSteps) : 0;
+  tc8::xcorr_tc8_kernel<EB><<<static_cast<int>(2 * clusters), tc8::kThreads, smem, stream>>>(L);
+  return cudaGetLastError();
+}
+
 template <int EB>
 cudaError_t launch_pair(const CUtensorMap* tmap_i, const CUtensorMap* tmap_j, TcParams prm, int max_ctas,
                         cudaStream_t stream, int* kernels) {
   *kernels = 0;
-  constexpr int smem = tc8::Geo<EB>::kSmemBytes;
-  cudaError_t e = cudaFuncSetAttribute(tc8::xcorr_tc8_kernel<EB>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
-  if (e != cudaSuccess) return e;
-  // clusters that can be resident at once (pairs of SMs), asked once per process
-  static int resident_clusters = -1;
-  if (resident_clusters < 0) {
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(2, 1, 1);
-    cfg.blockDim = dim3(tc8::kThreads, 1, 1);
-    cfg.dynamicSmemBytes = smem;
-    int n = 0;
-    if (cudaOccupancyMaxActiveClusters(&n, tc8::xcorr_tc8_kernel<EB>, &cfg) != cudaSuccess || n < 1) {
-      cudaGetLastError();
-      n = 0;
-    }
-    resident_clusters = n;
-  }
-  const long long units = static_cast<long long>(prm.C) * tc8::pairs_per_channel(prm.nt);
-  if (units > 0x7FFFFFFFLL) return cudaErrorInvalidValue;
-  prm.units = static_cast<int>(units);
-  long long clusters = max_ctas / 2;
-  if (resident_clusters > 0 && resident_clusters < clusters) clusters = resident_clusters;
-  if (units < clusters) clusters = units;
-  if (clusters < 1) clusters = 1;
-  prm.split_parts = prm.split_ws ? tc8::split_parts(units, clusters, prm.nks, tc8::Geo<EB>::kSteps) : 0;
-  prm.acc_pairs = static_cast<long long>(prm.C) * prm.N * (prm.N + 1) / 2;
-  prm.ws_pairs = prm.split_ws ? static_cast<long long>(split_workspace_bytes(max_ctas) / sizeof(int2)) : 0;
-  tc8::xcorr_tc8_kernel<EB><<<static_cast<int>(2 * clusters), tc8::kThreads, smem, stream>>>(*tmap_i, *tmap_j, prm);
-  e = cudaGetLastError();
+  tc8::PairLaunch L = {};
+  L.nprob = 1;
+  set_problem(L, 0, *tmap_i, *tmap_j, prm);
+  const long long units = static_cast<long long>(prm.C) * L.p[0].per_chan;
+  L.prefix[0] = 0;
+  L.prefix[1] = static_cast<int>(units < 0x7FFFFFFFLL ? units : 0x7FFFFFFFLL);
+  L.split_ws = prm.split_ws;
+  L.ws_pairs = prm.split_ws ? static_cast<long long>(split_workspace_bytes(max_ctas) / sizeof(int2)) : 0;
+  L.timeout_ns = prm.timeout_ns;
+  long long clusters = 0;
+  cudaError_t e = launch_table<EB>(L, units, max_ctas, stream, &clusters);
   if (e != cudaSuccess) return e;
   *kernels = 1;
-  if (prm.split_parts > 0) {
+  if (L.split_parts > 0) {
     tc8::CombineParams q;
     q.N = prm.N;
     q.nt = prm.nt;
-    q.per_chan = tc8::pairs_per_channel(prm.nt);
-    q.units = prm.units;
+    q.per_chan = L.p[0].per_chan;
+    q.units = L.units;
     q.ncl = static_cast<int>(clusters);
-    q.q = prm.split_parts;
+    q.q = L.split_parts;
     q.accumulate = prm.accumulate;
     q.acc = prm.acc;
     q.ws = prm.split_ws;
-    q.acc_pairs = prm.acc_pairs;
-    q.ws_pairs = prm.ws_pairs;
+    q.acc_pairs = L.p[0].acc_pairs;
+    q.ws_pairs = L.ws_pairs;
     q.err = prm.err;
-    const int L = static_cast<int>(units % clusters);
-    tc8::split_combine_kernel<<<dim3(2 * L, tc8::kTile / 8), 256, 0, stream>>>(q);
+    const int Lft = static_cast<int>(units % clusters);
+    tc8::split_combine_kernel<<<dim3(2 * Lft, tc8::kTile / 8), 256, 0, stream>>>(q);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     *kernels = 2;
@@ -1482,6 +1560,29 @@ cudaError_t launch_xcorr_pair(int eb, const CUtensorMap* tmap_i, const CUtensorM
                               int max_ctas, cudaStream_t stream, int* kernels) {
   return eb == 1 ? launch_pair<1>(tmap_i, tmap_j, prm, max_ctas, stream, kernels)
                  : launch_pair<2>(tmap_i, tmap_j, prm, max_ctas, stream, kernels);
+}
+
+cudaError_t launch_xcorr_batch(const BatchProblem* probs, int n, int max_ctas, cudaStream_t stream, int* kernels) {
+  *kernels = 0;
+  if (n < 1 || n > kMaxBatch) return cudaErrorInvalidValue;
+  tc8::PairLaunch L = {};
+  L.nprob = n;
+  long long units = 0;
+  for (int k = 0; k < n; ++k) {
+    if (probs[k].prm.split_ws != nullptr || probs[k].prm.nks > 32768 / tc8::kStep) return cudaErrorInvalidValue;
+    set_problem(L, k, probs[k].ti, probs[k].tj, probs[k].prm);
+    L.prefix[k] = static_cast<int>(units);
+    units += static_cast<long long>(probs[k].prm.C) * L.p[k].per_chan;
+    if (units > 0x7FFFFFFFLL) return cudaErrorInvalidValue;
+  }
+  L.prefix[n] = static_cast<int>(units);
+  L.split_ws = nullptr;
+  L.ws_pairs = 0;
+  L.timeout_ns = probs[0].prm.timeout_ns;
+  long long clusters = 0;
+  cudaError_t e = launch_table<1>(L, units, max_ctas, stream, &clusters);
+  if (e == cudaSuccess) *kernels = 1;
+  return e;
 }
 
 }  // namespace xe

@@ -17,6 +17,7 @@ from . import xengine as _xe
 
 XE_SERVICE_DRYRUN = 1
 XE_SERVICE_MANUAL = 2
+XE_SERVICE_NO_BATCH = 4
 XE_FAULT_LAUNCH = 1
 XE_FAULT_DROP_GULP = 2
 
@@ -37,7 +38,7 @@ class StreamStats(ctypes.Structure):
     _fields_ = [("committed", _LL), ("skipped_full", _LL), ("dropped", _LL), ("launches", _LL),
                 ("gulps_correlated", _LL), ("integrations", _LL), ("max_batch", _LL),
                 ("device_bytes", _LL), ("host_bytes", _LL), ("state", _I), ("pending", _I),
-                ("inflight", _I)]
+                ("inflight", _I), ("shared_launches", _LL)]
 
 
 def _setup(lib: ctypes.CDLL) -> None:
@@ -74,8 +75,10 @@ class ServiceError(_xe.XEngineError):
 class Service:
     """One xe_service; streams are added with ``add_stream``."""
 
-    def __init__(self, mem_cap_bytes: int = 0, dryrun: bool = False, manual: bool = False):
-        flags = (XE_SERVICE_DRYRUN if dryrun else 0) | (XE_SERVICE_MANUAL if manual else 0)
+    def __init__(self, mem_cap_bytes: int = 0, dryrun: bool = False, manual: bool = False,
+                 batch: bool = True):
+        flags = ((XE_SERVICE_DRYRUN if dryrun else 0) | (XE_SERVICE_MANUAL if manual else 0) |
+                 (0 if batch else XE_SERVICE_NO_BATCH))
         h = _P()
         self._check(_lib.xe_service_create(ctypes.byref(h), int(mem_cap_bytes), flags), "xe_service_create", None)
         self.handle = h

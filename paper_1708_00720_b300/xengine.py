@@ -80,6 +80,7 @@ def _load(debug: bool = False) -> ctypes.CDLL:
         "xe_plan_last_error": ([P], ctypes.c_char_p),
         "xe_version": ([], ctypes.c_char_p),
         "xe_probe_dp4a_rate": ([I, I, P, P, ctypes.POINTER(LL), P], I),
+        "xe_correlate_batch": ([I, P, P, P, P, P], I),
     }
     for name, (args, res) in sigs.items():
         fn = getattr(lib, name)
@@ -173,6 +174,17 @@ def xe_unpack(plan, d_packed, d_ci8, ntime: int, stream=None) -> None:
 def xe_correlate(plan, d_gulp, ntime: int, accumulate: int = 0, stream=None) -> None:
     _check(_lib.xe_correlate(plan, _ptr(d_gulp), ntime, accumulate, _stream(stream)),
            "xe_correlate", plan)
+
+
+def xe_correlate_batch(plans, gulps, ntimes, accumulates, stream=None) -> None:
+    """One launch correlating gulps[k] (ntimes[k] samples) into plans[k]."""
+    n = len(plans)
+    arr_p = (ctypes.c_void_p * n)(*plans)
+    arr_g = (ctypes.c_void_p * n)(*[_ptr(g) for g in gulps])
+    arr_t = (ctypes.c_int * n)(*[int(t) for t in ntimes])
+    arr_a = (ctypes.c_int * n)(*[int(a) for a in accumulates])
+    _check(_lib.xe_correlate_batch(n, arr_p, arr_g, arr_t, arr_a, _stream(stream)), "xe_correlate_batch",
+           plans[0] if n else None)
 
 
 def xe_integrate(plan, d_vis, stream=None) -> None:

@@ -173,4 +173,6 @@ def test_serving_workload_shapes_bit_exact(sv):
         np.testing.assert_array_equal(r["vis"][chans], want)
         s.release(sid, 0)
         assert s.stats(sid)["state"] == 0
+    print("\nlaunches shared between streams:", [s.stats(sid)["shared_launches"] for sid in ids],
+          "of", [s.stats(sid)["launches"] for sid in ids])
     s.close()

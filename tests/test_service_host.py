@@ -207,3 +207,44 @@ def test_service_needs_a_gpu_outside_dry_run(gpu_available):
         pytest.skip("a GPU is present")
     with pytest.raises(xe.XEngineError):
         sv.Service()
+
+
+def test_ready_gulps_of_several_streams_share_a_launch():
+    # two e4m3 streams and one int32 stream with in-flight work held (manual
+    # dry run); once all of it completes at the same time, the e4m3 streams'
+    # next runs go in ONE launch, the int32 stream's alone
+    s = mk()
+    a = s.add_stream(64, 8, 128, ring_gulps=8, integrate_gulps=1)
+    b = s.add_stream(128, 4, 256, ring_gulps=8, integrate_gulps=1)
+    c = s.add_stream(64, 8, 128, ring_gulps=8, integrate_gulps=1, operand="int32")
+    for q in range(3):                       # two launches in flight each, one gulp pending
+        for sid in (a, b, c):
+            put(s, sid, q)
+    for sid in (a, b, c):
+        st = s.stats(sid)
+        assert (st["inflight"], st["pending"], st["shared_launches"]) == (2, 1, 0)
+    s.dryrun_complete(-1)
+    sa, sb, sc = s.stats(a), s.stats(b), s.stats(c)
+    assert sa["shared_launches"] == 1 and sb["shared_launches"] == 1 and sc["shared_launches"] == 0
+    assert sa["launches"] == sb["launches"] == sc["launches"] == 3
+    for sid in (a, b, c):
+        assert s.stats(sid)["pending"] == 0
+        for idx in range(3):
+            s.dryrun_complete(sid)
+            r = s.poll(sid, timeout_ms=1000)
+            assert (r["index"], r["gulps"], r["skipped"]) == (idx, 1, 0)
+            s.release(sid, idx)
+    s.close()
+
+
+def test_no_batch_flag_keeps_launches_to_one_stream():
+    s = sv.Service(mem_cap_bytes=1 << 34, dryrun=True, manual=True, batch=False)
+    a = s.add_stream(64, 8, 128, ring_gulps=8, integrate_gulps=1)
+    b = s.add_stream(64, 8, 128, ring_gulps=8, integrate_gulps=1)
+    for q in range(3):
+        for sid in (a, b):
+            put(s, sid, q)
+    s.dryrun_complete(-1)
+    assert s.stats(a)["shared_launches"] == 0 and s.stats(b)["shared_launches"] == 0
+    assert s.stats(a)["launches"] == 3 and s.stats(b)["launches"] == 3
+    s.close()

@@ -361,3 +361,78 @@ def test_maximum_inputs_sampled(xe, operand):
     sampled_check(v, x, np.random.default_rng(3))
     for i, j in ((8191, 0), (8191, 8191), (4096, 4095), (128, 127), (8191, 8064)):
         assert tuple(v[0, oracle.tri_index(i, j)]) == oracle.correlate_one(x, 0, i, j)
+
+
+# ----------------------------------------------------- batched launches
+def test_batched_launch_of_several_problems(xe):
+    """Four problems of different array sizes (ragged tiles, a transposed odd
+    tile, more units than clusters) in ONE launch, one of them accumulating
+    onto an earlier gulp: each plan's visibilities equal the oracle's."""
+    import torch
+    shapes = [(512, 8, 1024), (272, 5, 333), (144, 3, 2048), (1024, 2, 256)]
+    engs, xs, gs = [], [], []
+    for k, (N, C, T) in enumerate(shapes):
+        engs.append(xe.XEngine(N, C, 2 * T, "fp8"))
+        xs.append(synth.voltages(N, C, T, seed=90 + k, random_phase=True))
+        gs.append(torch.from_numpy(xs[-1]).cuda())
+    # plan 2 already holds an earlier gulp; the batch adds to it
+    x_prev = synth.voltages(144, 3, 700, seed=99, random_phase=True)
+    engs[2].correlate(torch.from_numpy(x_prev).cuda())
+    launches0 = [xe.xe_plan_launch_count(e.plan) for e in engs]
+    acc = [0, 0, 1, 0]
+    xe.xe_correlate_batch([e.plan for e in engs], gs, [g.shape[0] for g in gs], acc)
+    torch.cuda.synchronize()
+    for k, e in enumerate(engs):
+        e.check()
+        assert xe.xe_plan_launch_count(e.plan) == launches0[k] + 1
+        got = e.integrate().cpu().numpy().astype(np.int64)
+        want = oracle.correlate(xs[k])
+        if acc[k]:
+            want = want + oracle.correlate(x_prev)
+            assert e.samples() == 700 + shapes[k][2]
+        np.testing.assert_array_equal(got, want)
+        e.close()
+
+
+def test_batched_launch_matches_single_launches_at_lwa_scale(xe):
+    """Two 512-input problems of 64 channels each (the shapes the serving
+    workload batches): one batched launch equals two plan calls."""
+    import torch
+    x1 = synth.voltages(512, 64, 1024, seed=95, random_phase=True)
+    x2 = synth.voltages(256, 64, 1024, seed=96, random_phase=True)
+    e1, e2 = xe.XEngine(512, 64, 1024, "fp8"), xe.XEngine(256, 64, 1024, "fp8")
+    g1, g2 = torch.from_numpy(x1).cuda(), torch.from_numpy(x2).cuda()
+    xe.xe_correlate_batch([e1.plan, e2.plan], [g1, g2], [1024, 1024], [0, 0])
+    v1, v2 = e1.integrate().cpu().numpy(), e2.integrate().cpu().numpy()
+    e1.check(); e2.check()
+    np.testing.assert_array_equal(v1, run(xe, x1, "fp8"))
+    np.testing.assert_array_equal(v2, run(xe, x2, "fp8"))
+    sampled_check(v1.astype(np.int64), x1, np.random.default_rng(4), nsamp=300)
+    e1.close(); e2.close()
+
+
+def test_batched_launch_argument_errors(xe):
+    import ctypes
+    import torch
+    lib = xe.library()
+    e8 = xe.XEngine(128, 2, 40000, "fp8")
+    e16 = xe.XEngine(128, 2, 64, "fp16")
+    g = torch.zeros((40000, 2, 128), dtype=torch.uint8, device="cuda")
+    s = torch.cuda.current_stream().cuda_stream
+
+    def call(plans, T, acc=0):
+        n = len(plans)
+        P = (ctypes.c_void_p * max(n, 1))(*plans)
+        G = (ctypes.c_void_p * max(n, 1))(*([g.data_ptr()] * n))
+        Ts = (ctypes.c_int * max(n, 1))(*([T] * n))
+        A = (ctypes.c_int * max(n, 1))(*([acc] * n))
+        return lib.xe_correlate_batch(n, P, G, Ts, A, s)
+
+    assert call([], 64) == xe.XE_ERR_INVALID_ARG
+    assert call([e8.plan] * 9, 64) == xe.XE_ERR_INVALID_ARG
+    assert call([e8.plan, e8.plan], 64) == xe.XE_ERR_INVALID_ARG          # one plan twice
+    assert call([e8.plan, e16.plan], 64) == xe.XE_ERR_INVALID_ARG         # not e4m3
+    assert call([e8.plan], 40000) == xe.XE_ERR_SHAPE                      # more than one launch
+    assert call([e8.plan], 64, acc=2) == xe.XE_ERR_INVALID_ARG
+    assert xe.xe_plan_launch_count(e8.plan) == 0
+    e8.close(); e16.close()
