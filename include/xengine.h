@@ -311,7 +311,9 @@ XE_API xe_status xe_calib_scale(xe_calib_t calib, const float *d_in, const doubl
  * and commits it with its sequence number (strictly increasing; gaps are
  * gulps that never arrived).  Committed gulps are copied to the device ring
  * at once; pending gulps that are contiguous in the ring are correlated in
- * one launch whenever the stream has fewer than two launches in flight.
+ * one launch whenever the stream has fewer than two launches in flight and
+ * the GPU fewer than two in all (an idle GPU takes a gulp at once; a busy
+ * one lets ready gulps gather).
  * When several e4m3 streams have such runs ready at the same time (each of
  * at most 32768 samples), their runs share ONE launch (xe_correlate_batch)
  * on the service's own CUDA stream, up to 8 streams per launch; each

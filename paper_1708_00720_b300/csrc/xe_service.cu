@@ -17,9 +17,11 @@
 // A committed gulp is copied to its device slot at once.  The dispatcher
 // launches the correlation of every pending gulp that is contiguous in the
 // ring and belongs to the current integration as ONE launch, as soon as the
-// stream has fewer than two launches in flight: with an idle GPU each gulp
-// goes alone (lowest latency); with a busy GPU gulps queue up and go together
-// (fewer, larger launches).  When an integration's last gulp has been dispatched (or
+// stream has fewer than two launches in flight and the GPU fewer than two in
+// all: with an idle GPU each gulp goes alone (lowest latency); with a busy
+// GPU gulps queue up and go together (fewer, larger launches), and the runs
+// of several e4m3 streams that are ready at once share one launch of the
+// pair kernel (xe_correlate_batch).  When an integration's last gulp has been dispatched (or
 // on flush) the accumulator is emitted into a free output slot and copied to
 // host memory; completion times come from host callbacks enqueued after the
 // copies.  Ring slots are recycled when the launch that read them completes.
@@ -61,6 +63,10 @@ double now_ms() {
 
 constexpr int kOutSlots = 2;     // pinned output buffers per stream
 constexpr int kMaxInflight = 2;  // correlate launches in flight per stream
+// ... and on the whole GPU: with the GPU busy, further ready gulps wait and
+// then go together, several streams in one launch (with it idle, a gulp
+// goes at once, alone)
+constexpr int kMaxInflightTotal = 2;
 
 enum SlotState : int { kFree = 0, kReserved, kCommitted, kDispatched };
 
@@ -75,6 +81,7 @@ struct Batch {
   int first_slot = 0, n = 0;
   cudaEvent_t done = nullptr;
   std::atomic<int> complete{0};
+  bool counts = false;   // the one batch of its launch that holds the service's in-flight count
 };
 
 // Gulps of one stream ready to go in one launch (see next_run).
@@ -144,6 +151,7 @@ struct ServiceImpl {
   long long cap = 0, used = 0;
   int flags = 0;
   bool batch = true;     // ready gulps of several e4m3 streams share one launch
+  int inflight_total = 0;   // launches in flight on the GPU (a shared launch counts once)
   cudaStream_t s_batch = nullptr;   // the shared launches
   int num_sms = 148;   // of the service's device; a dry run models a 148-SM B300
   bool dry = false, manual = false;
@@ -201,6 +209,7 @@ void retire(StreamImpl* s) {
   while (!s->inflight.empty() && s->inflight.front()->complete.load(std::memory_order_acquire)) {
     Batch* b = s->inflight.front().get();
     for (int k = 0; k < b->n; ++k) s->slot_state[(b->first_slot + k) % s->cfg.ring_gulps] = kFree;
+    if (b->counts) s->svc->inflight_total--;
     if (b->done) cudaEventDestroy(b->done);
     s->inflight.pop_front();
   }
@@ -273,7 +282,7 @@ bool try_emit(StreamImpl* s) {
 // belong to the current integration, if the stream may launch now.
 bool next_run(StreamImpl* s, Run* r) {
   if (s->state != XE_OK || s->pending.empty() || static_cast<int>(s->inflight.size()) >= kMaxInflight ||
-      s->emit_pending)
+      s->emit_pending || s->svc->inflight_total >= kMaxInflightTotal)
     return false;
   const int G = s->cfg.integrate_gulps;
   const long long integ = s->pending.front().seq / G;
@@ -306,6 +315,7 @@ void commit_run(StreamImpl* s, const Run& r, std::unique_ptr<Batch> b, bool shar
   if (shared) s->st.shared_launches++;
   s->st.gulps_correlated += r.n;
   if (r.n > s->st.max_batch) s->st.max_batch = r.n;
+  if (b->counts) s->svc->inflight_total++;
   s->inflight.push_back(std::move(b));
 }
 
@@ -316,6 +326,7 @@ void dispatch(StreamImpl* s) {
   auto b = std::make_unique<Batch>();
   b->first_slot = r.first;
   b->n = r.n;
+  b->counts = true;
   if (s->fault == XE_FAULT_LAUNCH) {
     s->fault = 0;
     fail_stream(s, XE_ERR_CUDA, "injected launch failure");
@@ -369,6 +380,7 @@ void dispatch_shared(ServiceImpl* svc) {
     bs[k] = std::make_unique<Batch>();
     bs[k]->first_slot = runs[k].first;
     bs[k]->n = runs[k].n;
+    bs[k]->counts = k == 0;
   }
   if (svc->dry) {
     if (!svc->manual)

@@ -210,26 +210,27 @@ def test_service_needs_a_gpu_outside_dry_run(gpu_available):
 
 
 def test_ready_gulps_of_several_streams_share_a_launch():
-    # two e4m3 streams and one int32 stream with in-flight work held (manual
-    # dry run); once all of it completes at the same time, the e4m3 streams'
-    # next runs go in ONE launch, the int32 stream's alone
+    # the GPU takes two launches in flight; further ready gulps wait, and when
+    # the GPU frees up the e4m3 streams' runs go in ONE launch, the int32
+    # stream's on its own (manual dry run: work completes on request)
     s = mk()
     a = s.add_stream(64, 8, 128, ring_gulps=8, integrate_gulps=1)
     b = s.add_stream(128, 4, 256, ring_gulps=8, integrate_gulps=1)
     c = s.add_stream(64, 8, 128, ring_gulps=8, integrate_gulps=1, operand="int32")
-    for q in range(3):                       # two launches in flight each, one gulp pending
-        for sid in (a, b, c):
-            put(s, sid, q)
-    for sid in (a, b, c):
-        st = s.stats(sid)
-        assert (st["inflight"], st["pending"], st["shared_launches"]) == (2, 1, 0)
+    put(s, a, 0)
+    put(s, b, 0)                              # two launches in flight: the GPU is busy
+    put(s, c, 0)
+    put(s, a, 1)
+    put(s, b, 1)
+    assert [s.stats(x)["inflight"] for x in (a, b, c)] == [1, 1, 0]
+    assert [s.stats(x)["pending"] for x in (a, b, c)] == [1, 1, 1]
     s.dryrun_complete(-1)
     sa, sb, sc = s.stats(a), s.stats(b), s.stats(c)
-    assert sa["shared_launches"] == 1 and sb["shared_launches"] == 1 and sc["shared_launches"] == 0
-    assert sa["launches"] == sb["launches"] == sc["launches"] == 3
-    for sid in (a, b, c):
-        assert s.stats(sid)["pending"] == 0
-        for idx in range(3):
+    assert (sa["shared_launches"], sb["shared_launches"], sc["shared_launches"]) == (1, 1, 0)
+    assert (sa["launches"], sb["launches"], sc["launches"]) == (2, 2, 1)
+    assert sa["pending"] == sb["pending"] == sc["pending"] == 0
+    for sid, n in ((a, 2), (b, 2), (c, 1)):
+        for idx in range(n):
             s.dryrun_complete(sid)
             r = s.poll(sid, timeout_ms=1000)
             assert (r["index"], r["gulps"], r["skipped"]) == (idx, 1, 0)
@@ -241,10 +242,11 @@ def test_no_batch_flag_keeps_launches_to_one_stream():
     s = sv.Service(mem_cap_bytes=1 << 34, dryrun=True, manual=True, batch=False)
     a = s.add_stream(64, 8, 128, ring_gulps=8, integrate_gulps=1)
     b = s.add_stream(64, 8, 128, ring_gulps=8, integrate_gulps=1)
-    for q in range(3):
-        for sid in (a, b):
-            put(s, sid, q)
+    put(s, a, 0)
+    put(s, b, 0)
+    put(s, a, 1)
+    put(s, b, 1)
     s.dryrun_complete(-1)
     assert s.stats(a)["shared_launches"] == 0 and s.stats(b)["shared_launches"] == 0
-    assert s.stats(a)["launches"] == 3 and s.stats(b)["launches"] == 3
+    assert s.stats(a)["launches"] == 2 and s.stats(b)["launches"] == 2
     s.close()
