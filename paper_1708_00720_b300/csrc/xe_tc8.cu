@@ -396,24 +396,28 @@ struct ProbDev {
   long long acc_pairs;   // int2 elements of acc (debug index checks)
   int N, nt, per_chan, nks, accumulate;
 };
+// NP: table size, 1 for a plan's own launch (every index a constant) or
+// kMaxBatch for a batched launch.
+template <int NP>
 struct PairLaunch {
-  CUtensorMap ti[kMaxBatch];   // I tiles: box {128, 1, rows}, 128-byte swizzle
-  CUtensorMap tj[kMaxBatch];   // half J tiles: box {64, 1, rows}, 64-byte swizzle
-  ProbDev p[kMaxBatch];
-  int prefix[kMaxBatch + 1];
+  CUtensorMap ti[NP];   // I tiles: box {128, 1, rows}, 128-byte swizzle
+  CUtensorMap tj[NP];   // half J tiles: box {64, 1, rows}, 64-byte swizzle
+  ProbDev p[NP];
+  int prefix[NP + 1];
   int nprob, units, split_parts;
   int2* split_ws;              // time-sliced leftover units (one problem only), or nullptr
   long long ws_pairs;
   unsigned long long timeout_ns;
 };
-static_assert(sizeof(PairLaunch) <= 4096, "kernel parameter space");
+static_assert(sizeof(PairLaunch<kMaxBatch>) <= 4096, "kernel parameter space");
 static_assert(alignof(CUtensorMap) >= 64, "tensor maps in parameter space need 64-byte alignment");
 
 // A wait gave up: stop every role of this CTA and record the code in every
 // problem's error word (the launch's results are all in doubt).
-__device__ __forceinline__ void fail_all(const Smem& s, const PairLaunch& L, int code) {
+template <int NP>
+__device__ __forceinline__ void fail_all(const Smem& s, const PairLaunch<NP>& L, int code) {
   atomicExch(s.abort_flag, 1);
-  for (int k = 0; k < L.nprob; ++k) atomicOr(L.p[k].err, code);
+  for (int k = 0; k < (NP == 1 ? 1 : L.nprob); ++k) atomicOr(L.p[k].err, code);
 }
 
 // Schedule of this cluster in shared memory: {items, R, cl, ncl, nks} and
@@ -443,7 +447,8 @@ __device__ inline void fill_sched(int* sc, int units, int cl, int ncl, int nks, 
 
 // Item i of this cluster (the schedule is read from shared memory each time:
 // registers are scarce in every warp role), with its problem.
-__device__ __forceinline__ Item item_at(const int* sc, int i, const PairLaunch& L) {
+template <int NP>
+__device__ __forceinline__ Item item_at(const int* sc, int i, const PairLaunch<NP>& L) {
   Item w;
   const int R = sc[1];
   int g;
@@ -459,7 +464,8 @@ __device__ __forceinline__ Item item_at(const int* sc, int i, const PairLaunch& 
     w.lo = sc[8];
   }
   int p = 0;
-  while (p + 1 < L.nprob && g >= L.prefix[p + 1]) ++p;
+  if constexpr (NP > 1)
+    while (p + 1 < L.nprob && g >= L.prefix[p + 1]) ++p;
   w.p = p;
   w.u = g - L.prefix[p];
   if (w.k1 < 0) w.k1 = L.p[p].nks;
@@ -694,9 +700,9 @@ __device__ __forceinline__ int2 unbias(int2 raw, float rre, float rim, float cre
                    __float2int_rn(__fmaf_rn(__int_as_float(raw.y), kScale, rim + cim)));
 }
 
-template <int EB>
+template <int EB, int NP>
 __global__ void __cluster_dims__(2, 1, 1) __launch_bounds__(kThreads, 1)
-xcorr_tc8_kernel(const __grid_constant__ PairLaunch L) {
+xcorr_tc8_kernel(const __grid_constant__ PairLaunch<NP> L) {
   using G = Geo<EB>;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* base = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
@@ -730,7 +736,7 @@ xcorr_tc8_kernel(const __grid_constant__ PairLaunch L) {
     *s.abort_flag = 0;
     fill_sched(s.sched, L.units, cl, ncl, L.p[0].nks, G::kSteps, L.split_parts);
     mbar_fence_init();
-    for (int k = 0; k < L.nprob; ++k) {
+    for (int k = 0; k < (NP == 1 ? 1 : L.nprob); ++k) {
       tma_prefetch_desc(&L.ti[k]);
       tma_prefetch_desc(&L.tj[k]);
     }
@@ -1397,7 +1403,7 @@ xcorr_tc8_kernel(const __grid_constant__ PairLaunch L) {
   // and shared memory are read by it) before either CTA frees or leaves.
   if (warp == 1 && lane == 0) {
     if (!mbar_wait(s.final_bar, 0, lim))
-      for (int k = 0; k < L.nprob; ++k) atomicOr(L.p[k].err, kErrWaitFinal);
+      for (int k = 0; k < (NP == 1 ? 1 : L.nprob); ++k) atomicOr(L.p[k].err, kErrWaitFinal);
   }
   tc_fence_before();
   __syncthreads();
@@ -1463,7 +1469,7 @@ int tc8_smem_bytes(int eb) { return eb == 1 ? tc8::Geo<1>::kSmemBytes : tc8::Geo
 namespace {
 // Clusters (pairs of SMs) of the pair kernel that can be resident at once,
 // asked once per process and operand width.
-template <int EB>
+template <int EB, int NP>
 int resident_clusters() {
   static int n = -1;
   if (n < 0) {
@@ -1472,7 +1478,7 @@ int resident_clusters() {
     cfg.blockDim = dim3(tc8::kThreads, 1, 1);
     cfg.dynamicSmemBytes = tc8::Geo<EB>::kSmemBytes;
     int r = 0;
-    if (cudaOccupancyMaxActiveClusters(&r, tc8::xcorr_tc8_kernel<EB>, &cfg) != cudaSuccess || r < 1) {
+    if (cudaOccupancyMaxActiveClusters(&r, tc8::xcorr_tc8_kernel<EB, NP>, &cfg) != cudaSuccess || r < 1) {
       cudaGetLastError();
       r = 0;
     }
@@ -1482,7 +1488,8 @@ int resident_clusters() {
 }
 
 // Problem k of a launch description from a plan's parameters.
-void set_problem(tc8::PairLaunch& L, int k, const CUtensorMap& ti, const CUtensorMap& tj, const TcParams& prm) {
+template <int NP>
+void set_problem(tc8::PairLaunch<NP>& L, int k, const CUtensorMap& ti, const CUtensorMap& tj, const TcParams& prm) {
   L.ti[k] = ti;
   L.tj[k] = tj;
   tc8::ProbDev& d = L.p[k];
@@ -1496,22 +1503,23 @@ void set_problem(tc8::PairLaunch& L, int k, const CUtensorMap& ti, const CUtenso
   d.accumulate = prm.accumulate;
 }
 
-template <int EB>
-cudaError_t launch_table(tc8::PairLaunch& L, long long units, int max_ctas, cudaStream_t stream,
+template <int EB, int NP>
+cudaError_t launch_table(tc8::PairLaunch<NP>& L, long long units, int max_ctas, cudaStream_t stream,
                          long long* clusters_out) {
   constexpr int smem = tc8::Geo<EB>::kSmemBytes;
-  cudaError_t e = cudaFuncSetAttribute(tc8::xcorr_tc8_kernel<EB>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  cudaError_t e =
+      cudaFuncSetAttribute(tc8::xcorr_tc8_kernel<EB, NP>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
   if (e != cudaSuccess) return e;
   if (units > 0x7FFFFFFFLL) return cudaErrorInvalidValue;
   L.units = static_cast<int>(units);
   long long clusters = max_ctas / 2;
-  const int res = resident_clusters<EB>();
+  const int res = resident_clusters<EB, NP>();
   if (res > 0 && res < clusters) clusters = res;
   if (units < clusters) clusters = units;
   if (clusters < 1) clusters = 1;
   *clusters_out = clusters;
   L.split_parts = L.split_ws ? tc8::split_parts(units, clusters, L.p[0].nks, tc8::Geo<EB>::kSteps) : 0;
-  tc8::xcorr_tc8_kernel<EB><<<static_cast<int>(2 * clusters), tc8::kThreads, smem, stream>>>(L);
+  tc8::xcorr_tc8_kernel<EB, NP><<<static_cast<int>(2 * clusters), tc8::kThreads, smem, stream>>>(L);
   return cudaGetLastError();
 }
 
@@ -1519,7 +1527,7 @@ template <int EB>
 cudaError_t launch_pair(const CUtensorMap* tmap_i, const CUtensorMap* tmap_j, TcParams prm, int max_ctas,
                         cudaStream_t stream, int* kernels) {
   *kernels = 0;
-  tc8::PairLaunch L = {};
+  tc8::PairLaunch<1> L = {};
   L.nprob = 1;
   set_problem(L, 0, *tmap_i, *tmap_j, prm);
   const long long units = static_cast<long long>(prm.C) * L.p[0].per_chan;
@@ -1529,7 +1537,7 @@ cudaError_t launch_pair(const CUtensorMap* tmap_i, const CUtensorMap* tmap_j, Tc
   L.ws_pairs = prm.split_ws ? static_cast<long long>(split_workspace_bytes(max_ctas) / sizeof(int2)) : 0;
   L.timeout_ns = prm.timeout_ns;
   long long clusters = 0;
-  cudaError_t e = launch_table<EB>(L, units, max_ctas, stream, &clusters);
+  cudaError_t e = launch_table<EB, 1>(L, units, max_ctas, stream, &clusters);
   if (e != cudaSuccess) return e;
   *kernels = 1;
   if (L.split_parts > 0) {
@@ -1565,7 +1573,7 @@ cudaError_t launch_xcorr_pair(int eb, const CUtensorMap* tmap_i, const CUtensorM
 cudaError_t launch_xcorr_batch(const BatchProblem* probs, int n, int max_ctas, cudaStream_t stream, int* kernels) {
   *kernels = 0;
   if (n < 1 || n > kMaxBatch) return cudaErrorInvalidValue;
-  tc8::PairLaunch L = {};
+  tc8::PairLaunch<kMaxBatch> L = {};
   L.nprob = n;
   long long units = 0;
   for (int k = 0; k < n; ++k) {
@@ -1580,7 +1588,7 @@ cudaError_t launch_xcorr_batch(const BatchProblem* probs, int n, int max_ctas, c
   L.ws_pairs = 0;
   L.timeout_ns = probs[0].prm.timeout_ns;
   long long clusters = 0;
-  cudaError_t e = launch_table<1>(L, units, max_ctas, stream, &clusters);
+  cudaError_t e = launch_table<1, kMaxBatch>(L, units, max_ctas, stream, &clusters);
   if (e == cudaSuccess) *kernels = 1;
   return e;
 }
