@@ -4,8 +4,9 @@
 //   y[t][c][b] = sum_i w[c][b][i] x[t][c][i]
 //
 // This file holds the beamformer's C ABI, which sends up to 16 beams over up
-// to 512 inputs to the time-along-N kernel of xe_beam8.cu, and the
-// time-along-M kernel below for every other shape.
+// to 512 inputs to the e4m3 kernel of xe_beam8.cu (voltages in tensor
+// memory, weight terms resident in shared memory), and the float16 kernel
+// below for every other shape.
 //
 // Per channel this is a complex matrix product Y (T x B) = X (T x N) W^T,
 // written as one real product on the tcgen05 tensor cores (kind::f16):
@@ -587,14 +588,14 @@ struct xe_beam {
   int N = 0, C = 0, B = 0, S = 0, max_ntime = 0;
   int num_sms = 0;
   bool weights_set = false;
-  // time along N (xe_beam8.cu) when B <= 16 and N <= 512, else time along M
-  bool t_on_n = false;
-  int S8 = 0;                   // 128-input stages of the time-along-N kernel
-  uint16_t* d_wt = nullptr;     // time along M: float16 operand tiles
-  float* d_bias = nullptr;      // [C][2B] (time along M) or [C][32] (time along N)
-  uint8_t* d_wa = nullptr;      // time along N: e4m3 operand-A images
-  float* d_sigma = nullptr;     // time along N: per-channel weight scale
-  float* d_osc = nullptr;       // time along N: 2^9 / sigma
+  // the e4m3 kernel (xe_beam8.cu) when B <= 16 and N <= 512, else the float16 one
+  bool e4m3 = false;
+  int S8 = 0;                   // 128-input stages of the e4m3 kernel
+  uint16_t* d_wt = nullptr;     // float16 kernel: operand tiles
+  float* d_bias = nullptr;      // [C][2B] (float16 kernel) or [C][32] (e4m3 kernel)
+  uint8_t* d_wa = nullptr;      // e4m3 kernel: weight-term images (operand B)
+  float* d_sigma = nullptr;     // e4m3 kernel: per-channel weight scale
+  float* d_osc = nullptr;       // e4m3 kernel: 2^9 / sigma
   int* d_err = nullptr;
   long long launches = 0;
   std::string last_error;
@@ -604,8 +605,8 @@ namespace {
 constexpr unsigned long long kBeamTimeoutNs = 2000000000ull;
 bool aligned_to(const void* p, uintptr_t a) { return (reinterpret_cast<uintptr_t>(p) & (a - 1)) == 0; }
 
-// One gulp through the time-along-N kernel (validated arguments).
-xe_status form_t_on_n(xe_beam* b, const uint8_t* d_gulp, int ntime, float* d_out, cudaStream_t stream) {
+// One gulp through the e4m3 kernel (validated arguments).
+xe_status form_e4m3(xe_beam* b, const uint8_t* d_gulp, int ntime, float* d_out, cudaStream_t stream) {
   CUtensorMap map;
   const unsigned long long dims[3] = {static_cast<unsigned long long>(b->N), static_cast<unsigned long long>(b->C),
                                       static_cast<unsigned long long>(ntime)};
@@ -664,10 +665,10 @@ XE_API xe_status xe_beam_create(xe_beam_t* out, int n_input, int n_chan, int n_b
   b->S = (n_input + 63) / 64;
   b->max_ntime = max_ntime;
   b->num_sms = sms;
-  b->t_on_n = n_beam <= 16 && n_input <= 512;
+  b->e4m3 = n_beam <= 16 && n_input <= 512;
   b->S8 = (n_input + 127) / 128;
   bool ok = true;
-  if (b->t_on_n) {
+  if (b->e4m3) {
     ok = cudaMalloc(&b->d_wa, static_cast<size_t>(n_chan) * 128 * 256 * b->S8) == cudaSuccess;
     ok = ok && cudaMalloc(&b->d_sigma, static_cast<size_t>(n_chan) * sizeof(float)) == cudaSuccess;
     ok = ok && cudaMalloc(&b->d_osc, static_cast<size_t>(n_chan) * sizeof(float)) == cudaSuccess;
@@ -711,7 +712,7 @@ XE_API xe_status xe_beam_set_weights(xe_beam_t b, const float* d_w, void* stream
   if (!b || !d_w) return XE_ERR_INVALID_ARG;
   if (!aligned_to(d_w, 8)) return XE_ERR_ALIGNMENT;
   const cudaError_t e =
-      b->t_on_n ? xe::launch_beam8_weights(d_w, b->N, b->C, b->B, b->S8, b->d_wa, b->d_sigma, b->d_osc, b->d_bias,
+      b->e4m3 ? xe::launch_beam8_weights(d_w, b->N, b->C, b->B, b->S8, b->d_wa, b->d_sigma, b->d_osc, b->d_bias,
                                            static_cast<cudaStream_t>(stream))
                 : xe::launch_beam_weights(d_w, b->N, b->C, b->B, b->S, b->d_wt, b->d_bias,
                                           static_cast<cudaStream_t>(stream));
@@ -728,7 +729,7 @@ XE_API xe_status xe_beam_form(xe_beam_t b, const uint8_t* d_gulp, int ntime, flo
   if (ntime == 0) return XE_OK;
   if (!d_gulp || !d_out) return XE_ERR_INVALID_ARG;
   if (!aligned_to(d_gulp, 16) || !aligned_to(d_out, 16)) return XE_ERR_ALIGNMENT;
-  if (b->t_on_n) return form_t_on_n(b, d_gulp, ntime, d_out, static_cast<cudaStream_t>(stream));
+  if (b->e4m3) return form_e4m3(b, d_gulp, ntime, d_out, static_cast<cudaStream_t>(stream));
   CUtensorMap map;
   const bool map4 = b->N % 64 == 0;   // whole 64-input chunks: one copy per 4 stages
   bool enc;

@@ -1,49 +1,58 @@
-// Phase-and-sum beamformer with time along the MMA's N dimension, for up to
-// 16 beams and 512 inputs (the DRX pipeline's beamformer, section "LWA
-// Sevilleta implementation", which works on the 4+4-bit samples):
+// Phase-and-sum beamformer for up to 16 beams and 512 inputs (the DRX
+// pipeline's beamformer, section "LWA Sevilleta implementation", which works
+// on the 4+4-bit samples):
 //   y[t][c][b] = sum_i w[c][b][i] x[t][c][i].
 //
-// Per channel, Y^T (2B x T) = W' X'^T as a real product: output row o = 2b
+// Per channel, Y (T x 2B) = X' W'^T as a real product: output o = 2b
 // (Re y_b) has the coefficient Re w on the real part of x_i and -Im w on its
-// imaginary part, row 2b + 1 (Im y_b) has Im w and Re w.  Time runs along
-// the MMA's N (128 samples per unit), so one tcgen05 MMA does
-// 128 x 128 x 32 multiply-adds; with time along M (weights as the N = 2B
-// side) an MMA did only 128 x 32 x 16 at nearly the same issue cost.
+// imaginary part, o = 2b + 1 (Im y_b) has Im w and Re w.  One tcgen05 MMA
+// (kind::f8f6f4, cta_group::1) does M = 128 samples x N = 128 weight rows x
+// K = 32 bytes.
 //
-// Operands, e4m3 (kind::f8f6f4), both exact:
-//  * voltages (operand B, shared memory, K-major, 128-byte swizzle): the
-//    nibble v in [-8, 7] becomes u = v + 8 = nibble XOR 8, whose e4m3 bit
-//    pattern is exactly u * 2^-9 (as in the X-engine);
-//  * weights (operand A, tensor memory): the float16-rounded coefficients,
-//    scaled by a per-channel power of two sigma so that the largest has
-//    magnitude in [128, 256), are split into four e4m3 terms,
-//    v = t0 + t1 2^-4 + t2 2^-8 + t3 2^-12, each term the residual so far
+// Operands, e4m3, both exact:
+//  * voltages (operand A, tensor memory): time sample t of a 128-sample unit
+//    is TMEM lane t, so a thread copies its own raw row with no
+//    transposition: the nibble v in [-8, 7] becomes u = v + 8 = nibble XOR 8,
+//    whose e4m3 bit pattern is exactly u * 2^-9 (as in the X-engine); per
+//    stage of 128 inputs the real parts fill K bytes 0-127 (columns 0-31)
+//    and the imaginary parts K bytes 128-255 (columns 32-63);
+//  * weights (operand B, shared memory, K-major with the 128-byte swizzle,
+//    resident for as long as a CTA works on the channel): the float16-rounded
+//    coefficients, scaled by a per-channel power of two sigma so that the
+//    largest has magnitude in [128, 256), split into four e4m3 terms
+//    v = t0 + t1 2^-4 + t2 2^-8 + t3 2^-12, each the residual so far
 //    truncated toward zero to four significant bits (or, below 2^-6, to the
 //    e4m3 subnormal grid 2^-9).  Every term takes at least four bit
 //    positions, so three already hold a float16 value exactly while they stay
 //    above the subnormal grid: every coefficient of at least 2^-18 of the
 //    channel's largest is exact, and any other errs by less than 2^-21 / sigma
-//    (below 2^-28 of the largest).  The M = 128 rows are
-//    row 32 q + 8 k + m = term k of output o = 8 q + m.
+//    (below 2^-28 of the largest).  Weight row n = 4 o + k is term k of
+//    output o (zero rows beyond 2B outputs), so D column 4 o + k holds it.
 // Accumulators are float32; the epilogue forms
-//   y_o = (D_o0 + 2^-4 D_o1 + 2^-8 D_o2 + 2^-12 D_o3) 2^9 / sigma - 8 sum_K coef,
-// one tcgen05.ld.16x256b giving each thread terms 0, 1 (lanes m, m + 8) and a
-// second one terms 2, 3 (lanes m + 16, m + 24) of the same output.
+//   y_o = (D_o0 + 2^-4 D_o1 + 2^-8 D_o2 + 2^-12 D_o3) 2^9 / sigma - 8 sum_K coef.
 //
-// Work: a unit is (channel, 128-sample time tile); each CTA of the persistent
-// grid takes a contiguous range of units, so it changes channel at most a
-// few times; the channel's weights (at most 128 rows x 1024 K bytes, 256
-// TMEM columns) are loaded into tensor memory when the channel changes,
-// after the last MMA of the previous channel has completed.
+// Why this way round.  Shared memory carries, per 128-input stage, the raw
+// tile in (TMA) and out (unpack) and the tensor core's operand-B reads:
+// 64 KB, against 96 KB when the voltages were the shared-memory operand
+// (their unpacked copy was written and read again).
+//
+// Work: a unit is (channel, 128-sample time tile); each CTA of the
+// persistent grid takes a contiguous range of units, so it changes channel
+// at most a few times.  A channel's weights (S stages x 32 KB, pre-swizzled
+// in global memory) arrive by one bulk copy when the last MMA of the
+// previous channel has completed, issued by the MMA thread (the voltage
+// producers carry on meanwhile).
 // Per CTA (448 threads):
 //   warp 0       TMA of raw tiles [128 samples][128 inputs] (16 KB, 128-byte
-//                swizzle), one per stage of 128 inputs
-//   warp 1       MMA issuer (one thread): 8 MMAs per stage, D double-buffered
-//   warps 2-9    unpack: 16-byte chunks of the raw tile -> re and im e4m3
-//                bytes of operand B (re of inputs 64a..64a+63 at K bytes
-//                0-63 of atom a, im at 64-127)
-//   warps 10-13  epilogue (TMEM lane quadrant = warp mod 4): weight loads
-//                into tensor memory, term combination, complex64 rows
+//                swizzle), one per stage
+//   warp 1       MMA issuer (one thread): 8 MMAs per stage, D double-buffered;
+//                at a channel change it waits for its own MMAs, copies the
+//                channel's weights in (one bulk copy) and prefetches the
+//                next channel's into L2
+//   warps 2-9    unpack: TMEM lane quadrant warp % 4, half (warp - 2) / 4 of
+//                the 16-byte chunks of each raw row -> tcgen05.st.32x32b
+//   warps 10-13  epilogue (TMEM lane quadrant = warp mod 4): terms combined,
+//                rows staged in shared memory, written as whole 128-byte lines
 // Every wait is bounded; on timeout the kernel records an error and returns.
 #include <cuda.h>
 #include <cuda_fp16.h>
@@ -57,49 +66,56 @@
 namespace xe {
 namespace b8 {
 
-constexpr int kTile = 128;                    // time samples per unit (MMA N)
+constexpr int kTile = 128;                    // time samples per unit (MMA M)
 constexpr int kStageIn = 128;                 // inputs per stage
 constexpr int kRawStage = kTile * kStageIn;   // 16 KB: [128 t][128 inputs], 128-byte swizzle
-constexpr int kAtom = kTile * 128;            // 16 KB: [128 t][128 K bytes], K-major, 128-byte swizzle
-constexpr int kOpStage = 2 * kAtom;           // K = 256 bytes per stage
+constexpr int kAtom = 128 * 128;              // 16 KB: [128 weight rows][128 K bytes], K-major, 128-byte swizzle
+constexpr int kWStage = 2 * kAtom;            // weights of one stage: K = 256 bytes (re part, im part)
+// Raw stages: 4 or 5 stages, or an L2 prefetch 2 or 3 stages ahead,
+// measured no faster than 3.
 constexpr int kRaw = 3;
-constexpr int kOp = 4;
-constexpr int kRows = 128;                    // MMA M: 4 terms x up to 32 outputs
-constexpr int kMaxStages = 4;                 // weights: 64 columns per stage in [0, 256) of tensor memory
+constexpr int kOp = 4;                        // voltage stages in tensor memory, 64 columns each
+constexpr int kRows = 128;                    // MMA N: 4 terms x up to 32 outputs
+constexpr int kMaxStages = 4;
 constexpr int kD0 = 256;                      // accumulators: [256, 384) and [384, 512)
 constexpr int kRawWarp = 0, kMmaWarp = 1, kUnpackWarp0 = 2, kUnpackWarps = 8;
 constexpr int kEpiWarp0 = kUnpackWarp0 + kUnpackWarps;
 constexpr int kThreads = 32 * (kEpiWarp0 + 4);
-constexpr int kNumBars = 2 * kRaw + 2 * kOp + 2 + 2 + 1 + 1;
-constexpr int kSmemBytes = kOp * kOpStage + kRaw * kRawStage + kNumBars * 8 + 16 + 1024;
+constexpr int kOutRow = 128;                  // staged output bytes per time row: 16 beams x complex64
+constexpr int kStageOut = 4 * 32 * kOutRow;   // 16 KB: the epilogue warps' rows
+constexpr int kNumBars = 2 * kRaw + 2 * kOp + 2 + 2 + 2 + 1;
+constexpr int kSmemBytes = kMaxStages * kWStage + kRaw * kRawStage + kStageOut + kNumBars * 8 + 16 + 1024;
 static_assert(kSmemBytes <= 227 * 1024, "shared memory budget");
-static_assert(kMaxStages * 64 <= kD0, "weight columns below the accumulators");
+static_assert(kOp * 64 <= kD0, "voltage columns below the accumulators");
 
 enum ErrCode : int {
   kErrRawFull = 1 << 0, kErrRawEmpty = 1 << 1, kErrOpFull = 1 << 2, kErrOpEmpty = 1 << 3,
-  kErrAccFull = 1 << 4, kErrAccEmpty = 1 << 5, kErrAFull = 1 << 6, kErrFinal = 1 << 7,
+  kErrAccFull = 1 << 4, kErrAccEmpty = 1 << 5, kErrWFull = 1 << 6, kErrFinal = 1 << 7, kErrWEmpty = 1 << 8,
 };
 
 struct Smem {
-  uint8_t* op;     // [kOp][2 atoms][128 t][128 K bytes]
+  uint8_t* w;      // [kMaxStages][2 atoms][128 rows][128 K bytes]  this channel's weights
   uint8_t* raw;    // [kRaw][128 t][128 bytes]
-  uint64_t *raw_full, *raw_empty, *op_full, *op_empty, *acc_full, *acc_empty, *a_full, *fin;
+  uint8_t* out;    // [4 warps][32 rows][128 bytes]  epilogue staging
+  uint64_t *raw_full, *raw_empty, *op_full, *op_empty, *acc_full, *acc_empty, *w_full, *w_empty, *fin;
   uint32_t* tmem_slot;
   int* abort_flag;
 };
 
 __device__ __forceinline__ Smem carve(uint8_t* base) {
   Smem s;
-  s.op = base;
-  s.raw = base + kOp * kOpStage;
-  uint64_t* b = reinterpret_cast<uint64_t*>(s.raw + kRaw * kRawStage);
+  s.w = base;
+  s.raw = base + kMaxStages * kWStage;
+  s.out = s.raw + kRaw * kRawStage;
+  uint64_t* b = reinterpret_cast<uint64_t*>(s.out + kStageOut);
   s.raw_full = b; b += kRaw;
   s.raw_empty = b; b += kRaw;
   s.op_full = b; b += kOp;
   s.op_empty = b; b += kOp;
   s.acc_full = b; b += 2;
   s.acc_empty = b; b += 2;
-  s.a_full = b; b += 1;
+  s.w_full = b; b += 1;
+  s.w_empty = b; b += 1;
   s.fin = b; b += 1;
   s.tmem_slot = reinterpret_cast<uint32_t*>(b);
   s.abort_flag = reinterpret_cast<int*>(b) + 1;
@@ -142,18 +158,6 @@ __device__ __forceinline__ uint64_t sdesc_k_sw128(uint32_t saddr) {
   return d;
 }
 
-// 16 lanes x 8 columns, 4 times along the columns: thread i gets lanes
-// base + i / 4 (regs 4 j, 4 j + 1) and base + i / 4 + 8 (4 j + 2, 4 j + 3)
-// at columns 8 j + 2 (i % 4) and 8 j + 2 (i % 4) + 1.
-__device__ __forceinline__ void tmem_ld_16x256b_x4(uint32_t taddr, uint32_t (&r)[16]) {
-  asm volatile(
-      "tcgen05.ld.sync.aligned.16x256b.x4.b32 "
-      "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-      : "r"(taddr));
-}
-
 // 32 lanes x 16 consecutive columns: thread `lane` writes row (quadrant base + lane).
 __device__ __forceinline__ void tmem_st_32x32b_x16(uint32_t taddr, const uint32_t (&r)[16]) {
   asm volatile(
@@ -164,25 +168,16 @@ __device__ __forceinline__ void tmem_st_32x32b_x16(uint32_t taddr, const uint32_
       : "memory");
 }
 
-// One channel's weight rows (this warp's TMEM lane quadrant) into tensor memory.
-__device__ __forceinline__ void load_weights(uint32_t tmem, int quad, int lane, const uint8_t* wa, int c,
-                                             int kbytes) {
-  const int row = 32 * quad + lane;
-  const uint4* src = reinterpret_cast<const uint4*>(wa + (static_cast<long long>(c) * kRows + row) * kbytes);
-  const uint32_t t_row = tmem + (static_cast<uint32_t>(32 * quad) << 16);
-  for (int cc = 0; cc < kbytes / 64; ++cc) {
-    uint32_t r[16];
-#pragma unroll
-    for (int k = 0; k < 4; ++k) {
-      const uint4 v = __ldg(src + 4 * cc + k);
-      r[4 * k] = v.x;
-      r[4 * k + 1] = v.y;
-      r[4 * k + 2] = v.z;
-      r[4 * k + 3] = v.w;
-    }
-    tmem_st_32x32b_x16(t_row + 16 * cc, r);
-  }
-  asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+// L2 prefetch of a global range (no shared-memory destination).
+__device__ __forceinline__ void bulk_prefetch_l2(const void* gmem_src, uint32_t bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(gmem_src), "r"(bytes) : "memory");
+}
+
+// Bulk copy global -> shared (no tensor map), completion on an mbarrier.
+__device__ __forceinline__ void bulk_load(void* smem_dst, const void* gmem_src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+               ::"r"(smem_u32(smem_dst)), "l"(gmem_src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
 }
 
 __global__ void __launch_bounds__(kThreads, 1)
@@ -193,8 +188,8 @@ beam8_kernel(const __grid_constant__ CUtensorMap tmap, const Beam8Params p) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const long long units = static_cast<long long>(p.C) * p.tiles;
   const long long u0 = units * blockIdx.x / gridDim.x, u1 = units * (blockIdx.x + 1) / gridDim.x;
-  const int S = p.S;                 // stages of 128 inputs, at most kMaxStages
-  const int kbytes = 256 * S;        // K bytes per weight row
+  const int S = p.S;                          // stages of 128 inputs, at most kMaxStages
+  const uint32_t wbytes = static_cast<uint32_t>(S) * kWStage;   // one channel's weights
   const uint64_t lim = p.timeout_ns;
   volatile int* abort_flag = s.abort_flag;
 
@@ -211,7 +206,8 @@ beam8_kernel(const __grid_constant__ CUtensorMap tmap, const Beam8Params p) {
       mbar_init(&s.acc_full[i], 1);
       mbar_init(&s.acc_empty[i], 4);
     }
-    mbar_init(s.a_full, 4);
+    mbar_init(s.w_full, 1);
+    mbar_init(s.w_empty, 1);
     mbar_init(s.fin, 1);
     *s.abort_flag = 0;
     mbar_fence_init();
@@ -252,21 +248,33 @@ beam8_kernel(const __grid_constant__ CUtensorMap tmap, const Beam8Params p) {
     // ------------------------------------------------------------ MMA issuer
     if (lane == 0) {
       // e4m3 x e4m3 -> f32, A from tensor memory, B K-major; M = 128, N = 128.
-      // Descriptors are one base per operand slot plus compile-time offsets
-      // and the slot and its phase are counters: the tensor core's
-      // instruction queue is short, so scalar work between MMAs shows.
       constexpr uint32_t idesc = (1u << 4) | ((128u >> 3) << 17) | ((128u >> 4) << 24);
-      constexpr uint32_t kSlotDesc = kOpStage >> 4, kAtomDesc = kAtom >> 4;   // descriptor address units
-      const uint64_t desc0 = sdesc_k_sw128(smem_u32(s.op));
+      constexpr uint32_t kWStageDesc = kWStage >> 4, kAtomDesc = kAtom >> 4;   // descriptor address units
+      const uint64_t wdesc0 = sdesc_k_sw128(smem_u32(s.w));
       int j = 0, wl = 0, os = 0;
       uint32_t oph = 0;                     // phase of operand slot os
       int prev_c = -1;
       bool ok = true;
       for (long long u = u0; u < u1 && ok; ++u, ++j) {
         const int c = static_cast<int>(u / p.tiles);
-        if (c != prev_c) {   // this channel's weights are in tensor memory
-          if (!wait_or_abort(s.a_full, wl & 1, lim, abort_flag)) {
-            if (!*abort_flag) fail(s, p.err, kErrAFull);
+        if (c != prev_c) {
+          // This thread loads the channel's weights: once the previous
+          // channel's MMAs (which read the old ones) have completed, one bulk
+          // copy; meanwhile the producers keep filling the voltage stages.
+          if (prev_c >= 0) {
+            mma_commit(s.w_empty);
+            if (!wait_or_abort(s.w_empty, (wl - 1) & 1, lim, abort_flag)) {
+              if (!*abort_flag) fail(s, p.err, kErrWEmpty);
+              break;
+            }
+          }
+          mbar_arrive_expect_tx(s.w_full, wbytes);
+          bulk_load(s.w, p.wa + static_cast<long long>(c) * wbytes, wbytes, s.w_full);
+          // the next channel of this CTA's range into L2 ahead of its copy
+          const long long un = (static_cast<long long>(c) + 1) * p.tiles;
+          if (un < u1) bulk_prefetch_l2(p.wa + (static_cast<long long>(c) + 1) * wbytes, wbytes);
+          if (!wait_or_abort(s.w_full, wl & 1, lim, abort_flag)) {
+            if (!*abort_flag) fail(s, p.err, kErrWFull);
             break;
           }
           ++wl;
@@ -286,8 +294,8 @@ beam8_kernel(const __grid_constant__ CUtensorMap tmap, const Beam8Params p) {
             break;
           }
           tc_fence_after();
-          const uint64_t bd = desc0 + static_cast<uint64_t>(kSlotDesc * os);
-          const uint32_t a0 = tmem + 64 * st;
+          const uint64_t bd = wdesc0 + static_cast<uint64_t>(kWStageDesc * st);
+          const uint32_t a0 = tmem + 64 * os;
           const uint32_t acc_first = st > 0 ? 1u : 0u;
 #pragma unroll
           for (int a = 0; a < 2; ++a)
@@ -309,11 +317,16 @@ beam8_kernel(const __grid_constant__ CUtensorMap tmap, const Beam8Params p) {
       if (!mbar_wait(s.fin, 0, lim)) atomicOr(p.err, kErrFinal);
     }
   } else if (warp < kEpiWarp0) {
-    // ------------------------------------------------------------ unpack
-    // Per stage each warp converts 16 time rows: 8 rows x 4 chunks per pass
-    // (rows r0 .. r0 + 7 in lanes 0-7 of each quarter: distinct swizzle
-    // phases, so the 16-byte loads and stores are conflict-free).
+    // ------------------------------------------------------------ unpack -> tensor memory
+    // Thread = TMEM lane = time row t of the unit (t = 32 quad + lane); this
+    // warp converts chunks 4 hf .. 4 hf + 3 (inputs 64 hf .. 64 hf + 63) of
+    // the row: real parts to columns 16 hf .. 16 hf + 15 of the stage,
+    // imaginary parts to 32 + 16 hf .. 32 + 16 hf + 15.  Within a quarter
+    // warp the rows have distinct swizzle phases: conflict-free loads.
     const int w8 = warp - kUnpackWarp0;
+    const int quad = warp & 3, hf = w8 >> 2;
+    const int t = 32 * quad + lane;
+    const uint32_t lane_off = static_cast<uint32_t>(32 * quad) << 16;
     int h = 0;
     bool ok = true;
     for (long long u = u0; u < u1 && ok; ++u) {
@@ -324,54 +337,46 @@ beam8_kernel(const __grid_constant__ CUtensorMap tmap, const Beam8Params p) {
           ok = false;
           break;
         }
+        const uint8_t* row = s.raw + rs * kRawStage + t * 128;
+        uint4 v[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          v[q] = *reinterpret_cast<const uint4*>(row + (((4 * hf + q) ^ (t & 7)) << 4));
+        uint32_t re[16], im[16];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+          const uint32_t x[4] = {v[q].x, v[q].y, v[q].z, v[q].w};
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            re[4 * q + k] = ((x[k] >> 4) & 0x0F0F0F0Fu) ^ 0x08080808u;
+            im[4 * q + k] = (x[k] & 0x0F0F0F0Fu) ^ 0x08080808u;
+          }
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(&s.raw_empty[rs]);   // the row is in registers
         if (h >= kOp && !wait_or_abort(&s.op_empty[os], ((h / kOp) & 1) ^ 1, lim, abort_flag)) {
           if (!*abort_flag) fail(s, p.err, kErrOpEmpty);
           ok = false;
           break;
         }
-        const uint8_t* raw = s.raw + rs * kRawStage;
-        uint8_t* op = s.op + os * kOpStage;
-#pragma unroll
-        for (int pass = 0; pass < 4; ++pass) {
-          const int r = 16 * w8 + 8 * (pass & 1) + (lane & 7);   // time row
-          const int jc = 4 * (pass >> 1) + (lane >> 3);           // 16-input chunk of the stage
-          const int ph = r & 7;
-          const uint4 x = *reinterpret_cast<const uint4*>(raw + r * 128 + ((jc ^ ph) << 4));
-          uint4 re, im;
-          re.x = ((x.x >> 4) & 0x0F0F0F0Fu) ^ 0x08080808u;
-          re.y = ((x.y >> 4) & 0x0F0F0F0Fu) ^ 0x08080808u;
-          re.z = ((x.z >> 4) & 0x0F0F0F0Fu) ^ 0x08080808u;
-          re.w = ((x.w >> 4) & 0x0F0F0F0Fu) ^ 0x08080808u;
-          im.x = (x.x & 0x0F0F0F0Fu) ^ 0x08080808u;
-          im.y = (x.y & 0x0F0F0F0Fu) ^ 0x08080808u;
-          im.z = (x.z & 0x0F0F0F0Fu) ^ 0x08080808u;
-          im.w = (x.w & 0x0F0F0F0Fu) ^ 0x08080808u;
-          const int q = jc & 3;
-          uint8_t* row = op + (jc >> 2) * kAtom + (r >> 3) * 1024 + ph * 128;
-          *reinterpret_cast<uint4*>(row + ((q ^ ph) << 4)) = re;
-          *reinterpret_cast<uint4*>(row + (((4 + q) ^ ph) << 4)) = im;
-        }
-        fence_proxy_async_smem();
+        const uint32_t ta = tmem + lane_off + 64 * os + 16 * hf;
+        tmem_st_32x32b_x16(ta, re);
+        tmem_st_32x32b_x16(ta + 32, im);
+        asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory");
+        tc_fence_before();
         __syncwarp();
-        if (lane == 0) {
-          mbar_arrive(&s.op_full[os]);
-          mbar_arrive(&s.raw_empty[rs]);
-        }
+        if (lane == 0) mbar_arrive(&s.op_full[os]);
       }
     }
   } else {
     // ------------------------------------------------------------ epilogue
+    // Thread = TMEM lane = time row t; D column 4 o + k is term k of output o.
     const int quad = warp & 3;
-    const int m = lane >> 2, o = 8 * quad + m;   // this thread's output row
     const int R = 2 * p.B;
+    uint8_t* stage = s.out + quad * (32 * kOutRow);
+    const int row_bytes = 8 * p.B;            // complex64 per beam
     int j = 0;
     bool ok = true;
-    if (u0 < u1) {
-      load_weights(tmem, quad, lane, p.wa, static_cast<int>(u0 / p.tiles), kbytes);
-      tc_fence_before();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(s.a_full);
-    }
     for (long long u = u0; u < u1 && ok; ++u, ++j) {
       const int c = static_cast<int>(u / p.tiles), t0 = static_cast<int>(u % p.tiles) * kTile;
       const int ab = j & 1;
@@ -381,43 +386,59 @@ beam8_kernel(const __grid_constant__ CUtensorMap tmap, const Beam8Params p) {
         break;
       }
       tc_fence_after();
-      if (u + 1 < u1 && static_cast<int>((u + 1) / p.tiles) != c) {
-        // every MMA of this channel has completed: the next channel's weights
-        load_weights(tmem, quad, lane, p.wa, c + 1, kbytes);
-        tc_fence_before();
-        __syncwarp();
-        if (lane == 0) mbar_arrive(s.a_full);
-        tc_fence_after();
-      }
       const float osc = p.osc[c];
-      const float bias = o < R ? p.bias[c * 32 + o] : 0.f;
-      float* out_c = p.out + static_cast<long long>(c) * R + o;
-      const long long row_stride = static_cast<long long>(p.C) * R;
-      const uint32_t t_lo = tmem + (static_cast<uint32_t>(32 * quad) << 16) + kD0 + 128 * ab;
-      const uint32_t t_hi = t_lo + (16u << 16);
-#pragma unroll 1
-      for (int ch = 0; ch < 4; ++ch) {
-        uint32_t lo[16], hi[16];
-        tmem_ld_16x256b_x4(t_lo + 32 * ch, lo);   // terms 0 (lane m) and 1 (lane m + 8)
-        tmem_ld_16x256b_x4(t_hi + 32 * ch, hi);   // terms 2 (lane m + 16) and 3 (lane m + 24)
+      const uint32_t t_row = tmem + (static_cast<uint32_t>(32 * quad) << 16) + kD0 + 128 * ab;
+      float y[32];
+#pragma unroll
+      for (int g = 0; g < 4; g += 2) {   // outputs 8 g .. 8 g + 15, two loads in flight
+        uint32_t v[32], w[32];
+        tmem_ld32(t_row + 32 * g, v);
+        tmem_ld32(t_row + 32 * g + 32, w);
         tmem_ld_wait();
-        if (o < R) {
 #pragma unroll
-          for (int blk = 0; blk < 4; ++blk)
-#pragma unroll
-            for (int e = 0; e < 2; ++e) {
-              float v = __uint_as_float(hi[4 * blk + 2 + e]) * 0.000244140625f;       // 2^-12
-              v = __fmaf_rn(__uint_as_float(hi[4 * blk + e]), 0.00390625f, v);         // 2^-8
-              v = __fmaf_rn(__uint_as_float(lo[4 * blk + 2 + e]), 0.0625f, v);         // 2^-4
-              v += __uint_as_float(lo[4 * blk + e]);
-              const int t = t0 + 32 * ch + 8 * blk + 2 * (lane & 3) + e;
-              if (t < p.T) out_c[t * row_stride] = __fmaf_rn(v, osc, -bias);
-            }
+        for (int e = 0; e < 8; ++e) {
+          float a = __uint_as_float(v[4 * e + 3]) * 0.000244140625f;       // 2^-12
+          a = __fmaf_rn(__uint_as_float(v[4 * e + 2]), 0.00390625f, a);     // 2^-8
+          a = __fmaf_rn(__uint_as_float(v[4 * e + 1]), 0.0625f, a);         // 2^-4
+          y[8 * g + e] = a + __uint_as_float(v[4 * e]);
+          float b = __uint_as_float(w[4 * e + 3]) * 0.000244140625f;
+          b = __fmaf_rn(__uint_as_float(w[4 * e + 2]), 0.00390625f, b);
+          b = __fmaf_rn(__uint_as_float(w[4 * e + 1]), 0.0625f, b);
+          y[8 * g + 8 + e] = b + __uint_as_float(w[4 * e]);
         }
       }
       tc_fence_before();
       __syncwarp();
-      if (lane == 0) mbar_arrive(&s.acc_empty[ab]);
+      if (lane == 0) mbar_arrive(&s.acc_empty[ab]);   // D read: the MMA may reuse it
+      // this row's outputs, scaled and unbiased, into its staging row as
+      // 16-byte chunks at position chunk XOR (row mod 8): the 32 rows of a
+      // warp then spread over all banks (rows are 128 bytes apart)
+      const float* bc = p.bias + c * 32;
+#pragma unroll
+      for (int k = 0; k < 8; ++k) {
+        const float4 bv = *reinterpret_cast<const float4*>(bc + 4 * k);
+        float4 val;
+        val.x = __fmaf_rn(y[4 * k + 0], osc, -bv.x);
+        val.y = __fmaf_rn(y[4 * k + 1], osc, -bv.y);
+        val.z = __fmaf_rn(y[4 * k + 2], osc, -bv.z);
+        val.w = __fmaf_rn(y[4 * k + 3], osc, -bv.w);
+        *reinterpret_cast<float4*>(stage + lane * kOutRow + ((k ^ (lane & 7)) << 4)) = val;
+      }
+      __syncwarp();
+      // the 32 rows of this warp, whole lines: lane k of each 8-lane group
+      // writes 16 bytes of row 4 pass + lane / 8
+      float* out_c = p.out + static_cast<long long>(c) * R;
+      const long long row_stride = static_cast<long long>(p.C) * R;   // floats per time row of out
+#pragma unroll 1
+      for (int r0 = 0; r0 < 32; r0 += 4) {
+        const int r = r0 + (lane >> 3), k16 = lane & 7;
+        const int tg = t0 + 32 * quad + r;
+        if (tg < p.T && 16 * k16 < row_bytes) {
+          const float4 val = *reinterpret_cast<const float4*>(stage + r * kOutRow + ((k16 ^ (r & 7)) << 4));
+          *reinterpret_cast<float4*>(out_c + tg * row_stride + 4 * k16) = val;
+        }
+      }
+      __syncwarp();
     }
   }
 
@@ -497,24 +518,28 @@ __device__ __forceinline__ uint32_t e4m3_bits(float x) {
   return sgn | (static_cast<uint32_t>(e + 7) << 3) | ((u >> 20) & 7u);
 }
 
-// Operand A images: [C][128 rows][2 Npad K bytes]; one thread per 4 K bytes.
+// Operand B images, laid out as shared memory holds them: per channel
+// [stage][re part, im part][128 rows][128 K bytes] with the 128-byte swizzle
+// (16-byte chunk q of row n at position q XOR (n mod 8)); row n = 4 o + k
+// holds term k of output o; K byte kb of a stage is input 128 stage + kb.
+// One thread per 4 K bytes.
 __global__ void beam8_image_kernel(const float2* __restrict__ w, int N, int C, int B, int S,
                                    const float* __restrict__ sigma, uint32_t* __restrict__ wa) {
-  const int kw = 64 * S;   // 32-bit words per row
   const long long idx = blockIdx.x * 256LL + threadIdx.x;
-  if (idx >= static_cast<long long>(C) * kRows * kw) return;
-  const int wd = static_cast<int>(idx % kw);
-  const int row = static_cast<int>((idx / kw) % kRows);
-  const int c = static_cast<int>(idx / (static_cast<long long>(kw) * kRows));
-  const int q = row >> 5, k = (row >> 3) & 3, o = 8 * q + (row & 7);
+  if (idx >= static_cast<long long>(C) * S * 2 * kRows * 32) return;
+  const int pw = static_cast<int>(idx & 31);                  // word of the 128-byte row (physical)
+  const int n = static_cast<int>((idx >> 5) % kRows);
+  const int part = static_cast<int>((idx >> 5) / kRows % 2);
+  const int st = static_cast<int>((idx >> 5) / (2 * kRows) % S);
+  const int c = static_cast<int>(idx / (32LL * kRows * 2 * S));
+  const int o = n >> 2, k = n & 3;
+  const int q = (pw >> 2) ^ (n & 7);                          // logical 16-byte chunk
   uint32_t word = 0;
   if (o < 2 * B) {
     const float sg = sigma[c];
 #pragma unroll
     for (int bt = 0; bt < 4; ++bt) {
-      const int K = 4 * wd + bt;                  // K byte: stage K / 256, atom (K / 128) & 1
-      const int kb = K & 127, part = kb >> 6;
-      const int i = (K >> 8) * kStageIn + ((K >> 7) & 1) * 64 + (kb & 63);
+      const int i = st * kStageIn + 16 * q + 4 * (pw & 3) + bt;
       if (i >= N) continue;
       float r = coef(w, N, B, c, o, i, part) * sg;   // exact: a power-of-two scaling
       float t = term4(r);
@@ -549,7 +574,7 @@ cudaError_t launch_beam8_weights(const float* w, int N, int C, int B, int S, uin
   b8::beam8_bias_kernel<<<(C * 32 + 255) / 256, 256, 0, stream>>>(w2, N, C, B, bias);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  const long long n = static_cast<long long>(C) * b8::kRows * 64 * S;
+  const long long n = static_cast<long long>(C) * S * 2 * b8::kRows * 32;
   b8::beam8_image_kernel<<<static_cast<unsigned>((n + 255) / 256), 256, 0, stream>>>(
       w2, N, C, B, S, sigma, reinterpret_cast<uint32_t*>(wa));
   return cudaGetLastError();

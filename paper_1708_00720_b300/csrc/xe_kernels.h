@@ -129,17 +129,18 @@ int beam_w_group(int B);   // stages of weights per bulk copy
 cudaError_t launch_beam_weights(const float* w, int N, int C, int B, int S, uint16_t* wt, float* bias,
                                 cudaStream_t stream);
 
-// Beamformer with time along the MMA's N (xe_beam8.cu), for B <= 16 beams
-// and N <= 512 inputs: operand A = the weights as four e4m3 terms per
-// float16 coefficient in tensor memory, operand B = the voltages as biased
-// e4m3 bytes.  The raw map views the gulp as uint8 {N, C, T} with box
-// {128, 1, 128} and the 128-byte swizzle.
+// Beamformer for B <= 16 beams and N <= 512 inputs (xe_beam8.cu): operand
+// A = the voltages as biased e4m3 bytes in tensor memory (a time sample per
+// lane), operand B = the weights as four e4m3 terms per float16 coefficient,
+// resident in shared memory per channel.  The raw map views the gulp as
+// uint8 {N, C, T} with box {128, 1, 128} and the 128-byte swizzle.
 struct Beam8Params {
   int N, C, B;            // inputs, channels, beams
   int S;                  // 128-input stages, ceil(N / 128) (<= 4)
   int T;                  // samples in this launch
   int tiles;              // 128-sample time tiles, ceil(T / 128)
-  const uint8_t* wa;      // [C][128 rows][256 S] e4m3 operand-A images (row 32 q + 8 k + m: term k of output 8 q + m)
+  const uint8_t* wa;      // [C][S][re, im][128 rows][128 K bytes] e4m3 operand-B images as shared memory holds
+                          // them (128-byte swizzle; row 4 o + k: term k of output o)
   const float* osc;       // [C] 2^9 / sigma_c
   const float* bias;      // [C][32] 8 * (sum of each output row's coefficients)
   float* out;             // [T][C][B] complex64
