@@ -180,6 +180,20 @@ __device__ __forceinline__ void bulk_load(void* smem_dst, const void* gmem_src, 
                : "memory");
 }
 
+// Channel and time tile of consecutive units, advanced without a 64-bit
+// division per unit.
+struct UnitPos {
+  int c, tile;
+  __device__ __forceinline__ UnitPos(long long u, int tiles)
+      : c(static_cast<int>(u / tiles)), tile(static_cast<int>(u % tiles)) {}
+  __device__ __forceinline__ void next(int tiles) {
+    if (++tile == tiles) {
+      tile = 0;
+      ++c;
+    }
+  }
+};
+
 __global__ void __launch_bounds__(kThreads, 1)
 beam8_kernel(const __grid_constant__ CUtensorMap tmap, const Beam8Params p) {
   extern __shared__ uint8_t smem_raw[];
@@ -227,8 +241,9 @@ beam8_kernel(const __grid_constant__ CUtensorMap tmap, const Beam8Params p) {
     if (lane == 0) {
       int h = 0;
       bool ok = true;
-      for (long long u = u0; u < u1 && ok; ++u) {
-        const int c = static_cast<int>(u / p.tiles), t0 = static_cast<int>(u % p.tiles) * kTile;
+      UnitPos up(u0, p.tiles);
+      for (long long u = u0; u < u1 && ok; ++u, up.next(p.tiles)) {
+        const int c = up.c, t0 = up.tile * kTile;
         for (int st = 0; st < S; ++st, ++h) {
           const int rs = h % kRaw;
           if (h >= kRaw && !wait_or_abort(&s.raw_empty[rs], ((h / kRaw) & 1) ^ 1, lim, abort_flag)) {
@@ -255,8 +270,9 @@ beam8_kernel(const __grid_constant__ CUtensorMap tmap, const Beam8Params p) {
       uint32_t oph = 0;                     // phase of operand slot os
       int prev_c = -1;
       bool ok = true;
-      for (long long u = u0; u < u1 && ok; ++u, ++j) {
-        const int c = static_cast<int>(u / p.tiles);
+      UnitPos up(u0, p.tiles);
+      for (long long u = u0; u < u1 && ok; ++u, ++j, up.next(p.tiles)) {
+        const int c = up.c;
         if (c != prev_c) {
           // This thread loads the channel's weights: once the previous
           // channel's MMAs (which read the old ones) have completed, one bulk
@@ -271,8 +287,8 @@ beam8_kernel(const __grid_constant__ CUtensorMap tmap, const Beam8Params p) {
           mbar_arrive_expect_tx(s.w_full, wbytes);
           bulk_load(s.w, p.wa + static_cast<long long>(c) * wbytes, wbytes, s.w_full);
           // the next channel of this CTA's range into L2 ahead of its copy
-          const long long un = (static_cast<long long>(c) + 1) * p.tiles;
-          if (un < u1) bulk_prefetch_l2(p.wa + (static_cast<long long>(c) + 1) * wbytes, wbytes);
+          if (u + (p.tiles - up.tile) < u1)
+            bulk_prefetch_l2(p.wa + (static_cast<long long>(c) + 1) * wbytes, wbytes);
           if (!wait_or_abort(s.w_full, wl & 1, lim, abort_flag)) {
             if (!*abort_flag) fail(s, p.err, kErrWFull);
             break;
@@ -377,8 +393,9 @@ beam8_kernel(const __grid_constant__ CUtensorMap tmap, const Beam8Params p) {
     const int row_bytes = 8 * p.B;            // complex64 per beam
     int j = 0;
     bool ok = true;
-    for (long long u = u0; u < u1 && ok; ++u, ++j) {
-      const int c = static_cast<int>(u / p.tiles), t0 = static_cast<int>(u % p.tiles) * kTile;
+    UnitPos up(u0, p.tiles);
+    for (long long u = u0; u < u1 && ok; ++u, ++j, up.next(p.tiles)) {
+      const int c = up.c, t0 = up.tile * kTile;
       const int ab = j & 1;
       if (!wait_or_abort(&s.acc_full[ab], (j >> 1) & 1, lim, abort_flag)) {
         if (!*abort_flag) fail(s, p.err, kErrAccFull);
