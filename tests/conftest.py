@@ -19,3 +19,15 @@ def pytest_configure(config):
 def gpu_available():
     import torch
     return torch.cuda.is_available()
+
+
+@pytest.hookimpl(trylast=True)   # after -m / -k have deselected
+def pytest_collection_modifyitems(session, config, items):
+    # the full-size oracle runs take minutes of host time: start them as soon
+    # as such tests are selected, so that they overlap the other GPU tests
+    if any(item.get_closest_marker("fullsize") for item in items):
+        import torch
+        if torch.cuda.is_available():
+            from tests import fullsize_oracle
+            fullsize_oracle.start("lwa")
+            fullsize_oracle.start("large_n")

@@ -6,14 +6,14 @@ triple-loop oracle once per module, in full, and every operand path's output
 of the benchmark's launch configuration (the fused one-gulp call) is compared
 with it element by element.  The 2048-input workload is compared in full on
 16 of its 64 channels (every baseline of those channels; the oracle's cost
-grows with N^2).  These cases take a few minutes of host time on the oracle;
-`-m "gpu and not fullsize"` skips them.
+grows with N^2).  These cases take minutes of host time on the oracle, which
+starts in a background thread as soon as they are collected
+(tests/fullsize_oracle.py); `-m "gpu and not fullsize"` skips them.
 """
 import numpy as np
 import pytest
 
-import oracle
-import synth
+from tests import fullsize_oracle
 
 pytestmark = [pytest.mark.gpu, pytest.mark.fullsize]
 
@@ -43,15 +43,12 @@ def emit(xe, x, operand):
 
 @pytest.fixture(scope="module")
 def lwa():
-    x = synth.config_voltages("lwa")
-    return x, oracle.correlate(x)
+    return fullsize_oracle.result("lwa")
 
 
 @pytest.fixture(scope="module")
 def large_n():
-    x = synth.config_voltages("large_n")
-    chans = np.arange(0, 64, 4)                       # 16 channels, spread over the band
-    return x, chans, oracle.correlate(np.ascontiguousarray(x[:, chans, :]))
+    return fullsize_oracle.result("large_n")     # 16 of the 64 channels
 
 
 @pytest.mark.parametrize("operand", ["fp8", "int32", "fp16"])
