@@ -109,15 +109,18 @@ def scaled_mm_fp8_tflops(dev, n: int = 8192, reps: int = 10):
         return None
 
 
-def recorded_traffic(kernel_key: str):
+def recorded_traffic(kernel_key: str, workload: str | None = None):
     """Per-launch DRAM bytes from the committed ncu summary, if it was taken on
-    the current kernel source; otherwise None."""
+    the current kernel source and (for the X-engine kernels) on this
+    workload; otherwise None."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(path):
         return None
     with open(path) as f:
         rec = json.load(f).get(kernel_key)
     if not rec or rec.get("source_hash") != source_hash(KERNEL_SOURCES[kernel_key]):
+        return None
+    if workload is not None and rec.get("workload_key") != workload:
         return None
     return rec.get("dram_bytes_per_launch")
 
@@ -1012,7 +1015,8 @@ def run_ours(args):
                 "unit": "TFLOP/s", "frac": (achieved / peak) if peak else None,
                 "scaled_mm_fp8_tflops": mm8,
                 "frac_of_scaled_mm_fp8": (achieved / mm8) if mm8 else None,
-                "traffic": recorded_traffic(key), "kernel": key, "kernel_ms": kern_ms,
+                "traffic": recorded_traffic(key, wl if not args.nchan else f"{wl} ({C} channels)"),
+                "kernel": key, "kernel_ms": kern_ms,
                 "kernel_ms_per_step": kern_stats,
                 "peak_source": peak_note,
                 "algorithmic_flops_per_launch": flops_per_launch}

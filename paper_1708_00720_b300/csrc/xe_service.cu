@@ -66,7 +66,10 @@ constexpr int kMaxInflight = 2;  // correlate launches in flight per stream
 // ... and on the whole GPU: with the GPU busy, further ready gulps wait and
 // then go together, several streams in one launch (with it idle, a gulp
 // goes at once, alone)
-constexpr int kMaxInflightTotal = 2;
+#ifndef XE_SVC_INFLIGHT_TOTAL
+#define XE_SVC_INFLIGHT_TOTAL 2
+#endif
+constexpr int kMaxInflightTotal = XE_SVC_INFLIGHT_TOTAL;
 
 enum SlotState : int { kFree = 0, kReserved, kCommitted, kDispatched };
 
