@@ -930,6 +930,8 @@ def run_ours(args):
         sms = torch.cuda.get_device_properties(dev).multi_processor_count
         peak_dp4a = rate * sms * mhz * 1e6 if mhz else None
         achieved_dp4a = step_cmac / (ms32 * 1e-3)
+        nb64 = (N + 63) // 64
+        issued_per_useful = nb64 * (nb64 + 1) // 2 * 64 * 64 / (N * (N + 1) / 2)
         int32_line = {"value": step_cmac / (ms32 * 1e-3) / 1e12, "unit": "cMAC TOPS",
                       "ms_per_step": ms32, "speedup_of_tensor_path": (step_cmac / (ms * 1e-3) / 1e12) /
                       (step_cmac / (ms32 * 1e-3) / 1e12),
@@ -937,6 +939,11 @@ def run_ours(args):
                                    "peak": peak_dp4a,
                                    "frac": (achieved_dp4a / peak_dp4a) if peak_dp4a else None,
                                    "dp4a_per_sm_clock": rate, "sm_mhz": mhz,
+                                   # dp4a issued per useful cMAC: whole 64 x 64 blocks, the
+                                   # upper halves of the diagonal ones included
+                                   "issued_per_useful": issued_per_useful,
+                                   "issued_frac": (achieved_dp4a * issued_per_useful / peak_dp4a)
+                                   if peak_dp4a else None,
                                    "peak_source": "measured dp4a issue rate (xe_probe_dp4a_rate) x SMs "
                                                   "x SM clock sampled during the int32 launch"}}
         e32.close()
@@ -1008,18 +1015,38 @@ def run_ours(args):
         key = "xcorr_tc_fp16"
     else:
         peak = None
-        peak_note = "CUDA-core path: no tensor peak"
         key = "xcorr_cudacore"
     mm8 = scaled_mm_fp8_tflops(dev) if args.operand == "fp8" else None
-    roofline = {"bound": "tensor" if peak else "alu", "achieved": achieved, "peak": peak,
-                "unit": "TFLOP/s", "frac": (achieved / peak) if peak else None,
-                "scaled_mm_fp8_tflops": mm8,
-                "frac_of_scaled_mm_fp8": (achieved / mm8) if mm8 else None,
-                "traffic": recorded_traffic(key, wl if not args.nchan else f"{wl} ({C} channels)"),
-                "kernel": key, "kernel_ms": kern_ms,
-                "kernel_ms_per_step": kern_stats,
-                "peak_source": peak_note,
-                "algorithmic_flops_per_launch": flops_per_launch}
+    traffic = recorded_traffic(key, wl if not args.nchan else f"{wl} ({C} channels)")
+    if peak:
+        roofline = {"bound": "tensor", "achieved": achieved, "peak": peak,
+                    "unit": "TFLOP/s", "frac": achieved / peak,
+                    "scaled_mm_fp8_tflops": mm8,
+                    "frac_of_scaled_mm_fp8": (achieved / mm8) if mm8 else None,
+                    "traffic": traffic, "kernel": key, "kernel_ms": kern_ms,
+                    "kernel_ms_per_step": kern_stats,
+                    "peak_source": peak_note,
+                    "algorithmic_flops_per_launch": flops_per_launch}
+    else:
+        # the CUDA-core path: one dp4a per useful complex MAC against the
+        # measured dp4a issue rate x SMs x the SM clock sampled while it ran
+        rate = xe.dp4a_rate_per_sm_clock(dev)
+        sms = torch.cuda.get_device_properties(dev).multi_processor_count
+        mhz = clk.summary()["sm_mhz"] or 0.0
+        peak_dp4a = rate * sms * mhz * 1e6 if mhz else None
+        achieved_dp4a = step_cmac / (kern_ms * 1e-3)
+        nb64 = (N + 63) // 64
+        issued_per_useful = nb64 * (nb64 + 1) // 2 * 64 * 64 / (N * (N + 1) / 2)
+        roofline = {"bound": "alu", "achieved": achieved_dp4a, "peak": peak_dp4a, "unit": "dp4a/s",
+                    "frac": (achieved_dp4a / peak_dp4a) if peak_dp4a else None,
+                    "issued_per_useful": issued_per_useful,
+                    "issued_frac": (achieved_dp4a * issued_per_useful / peak_dp4a) if peak_dp4a else None,
+                    "dp4a_per_sm_clock": rate, "sm_mhz": mhz,
+                    "traffic": traffic, "kernel": key, "kernel_ms": kern_ms,
+                    "kernel_ms_per_step": kern_stats,
+                    "peak_source": "measured dp4a issue rate (xe_probe_dp4a_rate) x SMs x SM clock "
+                                   "sampled during the timed region",
+                    "algorithmic_dp4a_per_launch": step_cmac}
 
     cpu = None
     if rank == 0 and world == 1 and not args.skip_cpu:

@@ -466,8 +466,9 @@ XE_API const char *xe_version(void);
  * multiply-accumulate.  Launches `ctas` CTAs of 256 threads; every thread
  * issues iters * 256 dp4a in 8 independent chains on register operands.
  * d_cycles[ctas] (int64) receives each CTA's clock64 cycles, d_sink[ctas *
- * 256] (int32) the threads' sums; *dp4a_per_cta is set on the host.  Rate
- * per SM and clock = dp4a_per_cta * (CTAs per SM) / cycles.  Asynchronous on
+ * 256] (int32) the threads' sums; *dp4a_per_cta is set on the host.  Launch
+ * one CTA per SM (ctas = the SM count; at most one is resident per SM): the
+ * rate per SM and clock is then dp4a_per_cta / cycles.  Asynchronous on
  * `stream`; XE_ERR_INVALID_ARG for iters outside 1..2^20, ctas outside
  * 1..2^16 or a NULL pointer.
  * ---------------------------------------------------------------------- */

@@ -4,15 +4,17 @@
 // triangle), computed with int8 4-way dot products (dp4a) on the CUDA cores:
 // two time samples of one input are packed as the int8 word
 //   w(t) = [a(t), b(t), a(t+1), b(t+1)]
-// and the rotated word of the other input as
-//   r(t) = [-b(t), a(t), -b(t+1), a(t+1)],
-// so that dp4a(w_i, w_j) adds a_i a_j + b_i b_j (Re) and dp4a(w_i, r_j) adds
+// and the rotated word of an I-side input as
+//   r(t) = [b(t), -a(t), b(t+1), -a(t+1)],
+// so that dp4a(w_i, w_j) adds a_i a_j + b_i b_j (Re) and dp4a(r_i, w_j) adds
 // b_i a_j - a_i b_j (Im) over two samples.
 //
-// Tiling: one CTA per (channel, 64 x 64 input block pair I >= J), 256
-// threads, each owning a 4 x 4 block of baselines in registers; 64-sample
-// chunks are read with 128-bit loads, unpacked once into shared memory and
-// prefetched one chunk ahead.
+// Tiling: one CTA of 128 threads per (channel, 64 x 64 input block pair
+// I >= J); each thread owns 4 I rows x 8 J columns in registers (64 int32
+// accumulators), so one pass over a time pair loads 16 words (four 128-bit
+// shared-memory loads, one wavefront each) for 64 dp4a.  64-sample chunks
+// are read with 128-bit global loads one chunk ahead and unpacked into
+// shared memory rows padded to 68 words (conflict-free 128-bit stores).
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -25,7 +27,8 @@ namespace cc {
 constexpr int kBlk = 64;       // inputs per block side
 constexpr int kChunk = 64;     // time samples per chunk
 constexpr int kPairs = kChunk / 2;
-constexpr int kThreads = 256;
+constexpr int kThreads = 128;
+constexpr int kRow = kBlk + 4; // words per shared-memory row (one time pair)
 
 __device__ __forceinline__ void tri_decode(int p, int& bi, int& bj) {
   int i = static_cast<int>((sqrtf(8.0f * p + 1.0f) - 1.0f) * 0.5f);
@@ -60,47 +63,53 @@ __device__ __forceinline__ void interleave(uint32_t A0, uint32_t B0, uint32_t A1
 __global__ void __launch_bounds__(kThreads)
 xcorr_cudacore_kernel(const uint8_t* __restrict__ x, int T, int C, int N,
                       int32_t* __restrict__ acc, int accumulate, int* err) {
-  __shared__ __align__(16) uint32_t si[kPairs][kBlk];
-  __shared__ __align__(16) uint32_t sj[kPairs][kBlk];
-  __shared__ __align__(16) uint32_t sr[kPairs][kBlk];
+  __shared__ __align__(16) uint32_t si[kPairs][kRow];   // I words
+  __shared__ __align__(16) uint32_t sr[kPairs][kRow];   // I rotated words
+  __shared__ __align__(16) uint32_t sj[kPairs][kRow];   // J words
 
   int bi, bj;
   tri_decode(blockIdx.x, bi, bj);
   const int tid = threadIdx.x;
-  const bool jside = tid >= 128;
-  const int lt = tid & 127;
-  const int lp = lt >> 2;          // time pair within the chunk
-  const int lq = lt & 3;           // 16-input chunk within the block
+  // unpack role: half the threads bring in I, half J; thread lt takes the
+  // 16-input chunk lq of time pairs lp and lp + 16
+  const bool jside = tid >= 64;
+  const int lt = tid & 63;
+  const int lp = lt >> 2;
+  const int lq = lt & 3;
   const int in0 = (jside ? bj : bi) * kBlk + lq * 16;
   const bool in_ok = in0 < N;      // N % 16 == 0: a 16-input chunk is all in or all out
-  const int ti = tid >> 4, tj = tid & 15;
+  // compute role: I rows 4 ti + a, J columns 4 tj + b and 32 + 4 tj + b
+  const int ti = tid >> 3, tj = tid & 7;
   const long long nbl = static_cast<long long>(N) * (N + 1) / 2;
 
   for (int c = blockIdx.y; c < C; c += gridDim.y) {
-    int re[4][4], im[4][4];
+    int re[4][8], im[4][8];
 #pragma unroll
     for (int a = 0; a < 4; ++a)
 #pragma unroll
-      for (int b = 0; b < 4; ++b) re[a][b] = im[a][b] = 0;
+      for (int b = 0; b < 8; ++b) re[a][b] = im[a][b] = 0;
 
-    auto load = [&](int t0, uint4& v0, uint4& v1) {
-      const int t = t0 + 2 * lp;
-      v0 = make_uint4(0, 0, 0, 0);
-      v1 = make_uint4(0, 0, 0, 0);
-      if (in_ok && t < T)
-        v0 = __ldg(reinterpret_cast<const uint4*>(x + (static_cast<size_t>(t) * C + c) * N + in0));
-      if (in_ok && t + 1 < T)
-        v1 = __ldg(reinterpret_cast<const uint4*>(x + (static_cast<size_t>(t + 1) * C + c) * N + in0));
+    // samples t0 + 2 lp (+1) and t0 + 2 lp + 32 (+1) of this thread's chunk
+    auto load = [&](int t0, uint4 (&v)[4]) {
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const int t = t0 + 2 * lp + (k & 1) + (k >> 1) * kPairs;
+        v[k] = make_uint4(0, 0, 0, 0);
+        if (in_ok && t < T)
+          v[k] = __ldg(reinterpret_cast<const uint4*>(x + (static_cast<size_t>(t) * C + c) * N + in0));
+      }
     };
 
-    uint4 v0, v1;
-    load(0, v0, v1);
+    uint4 v[4];
+    load(0, v);
     for (int t0 = 0; t0 < T; t0 += kChunk) {
       // unpack the prefetched chunk into shared memory
-      {
-        const uint32_t w0[4] = {v0.x, v0.y, v0.z, v0.w};
-        const uint32_t w1[4] = {v1.x, v1.y, v1.z, v1.w};
-        uint32_t* dst = jside ? &sj[lp][lq * 16] : &si[lp][lq * 16];
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int p = lp + h * (kPairs / 2);
+        const uint32_t w0[4] = {v[2 * h].x, v[2 * h].y, v[2 * h].z, v[2 * h].w};
+        const uint32_t w1[4] = {v[2 * h + 1].x, v[2 * h + 1].y, v[2 * h + 1].z, v[2 * h + 1].w};
+        uint32_t* dst = jside ? &sj[p][lq * 16] : &si[p][lq * 16];
 #pragma unroll
         for (int k = 0; k < 4; ++k) {
           const uint32_t A0 = sext_hi(w0[k]), B0 = sext_lo(w0[k]);
@@ -108,46 +117,48 @@ xcorr_cudacore_kernel(const uint8_t* __restrict__ x, int T, int C, int N,
           uint32_t o[4];
           interleave(A0, B0, A1, B1, o);
           *reinterpret_cast<uint4*>(dst + 4 * k) = make_uint4(o[0], o[1], o[2], o[3]);
-          if (jside) {
+          if (!jside) {
             uint32_t r[4];
-            interleave(__vsub4(0u, B0), A0, __vsub4(0u, B1), A1, r);
-            *reinterpret_cast<uint4*>(&sr[lp][lq * 16 + 4 * k]) = make_uint4(r[0], r[1], r[2], r[3]);
+            interleave(B0, __vsub4(0u, A0), B1, __vsub4(0u, A1), r);
+            *reinterpret_cast<uint4*>(&sr[p][lq * 16 + 4 * k]) = make_uint4(r[0], r[1], r[2], r[3]);
           }
         }
       }
       __syncthreads();
-      if (t0 + kChunk < T) load(t0 + kChunk, v0, v1);
-#pragma unroll 4
+      if (t0 + kChunk < T) load(t0 + kChunk, v);
+#pragma unroll 2
       for (int p = 0; p < kPairs; ++p) {
         const uint4 wi = *reinterpret_cast<const uint4*>(&si[p][ti * 4]);
-        const uint4 wj = *reinterpret_cast<const uint4*>(&sj[p][tj * 4]);
-        const uint4 wr = *reinterpret_cast<const uint4*>(&sr[p][tj * 4]);
+        const uint4 wr = *reinterpret_cast<const uint4*>(&sr[p][ti * 4]);
+        const uint4 wj0 = *reinterpret_cast<const uint4*>(&sj[p][tj * 4]);
+        const uint4 wj1 = *reinterpret_cast<const uint4*>(&sj[p][32 + tj * 4]);
         const int ai[4] = {static_cast<int>(wi.x), static_cast<int>(wi.y), static_cast<int>(wi.z),
                            static_cast<int>(wi.w)};
-        const int aj[4] = {static_cast<int>(wj.x), static_cast<int>(wj.y), static_cast<int>(wj.z),
-                           static_cast<int>(wj.w)};
         const int ar[4] = {static_cast<int>(wr.x), static_cast<int>(wr.y), static_cast<int>(wr.z),
                            static_cast<int>(wr.w)};
+        const int aj[8] = {static_cast<int>(wj0.x), static_cast<int>(wj0.y), static_cast<int>(wj0.z),
+                           static_cast<int>(wj0.w), static_cast<int>(wj1.x), static_cast<int>(wj1.y),
+                           static_cast<int>(wj1.z), static_cast<int>(wj1.w)};
 #pragma unroll
         for (int a = 0; a < 4; ++a)
 #pragma unroll
-          for (int b = 0; b < 4; ++b) {
+          for (int b = 0; b < 8; ++b) {
             re[a][b] = __dp4a(ai[a], aj[b], re[a][b]);
-            im[a][b] = __dp4a(ai[a], ar[b], im[a][b]);
+            im[a][b] = __dp4a(ar[a], aj[b], im[a][b]);
           }
       }
       __syncthreads();
     }
 
-    // write the lower-triangle part of this thread's 4 x 4 block
+    // write the lower-triangle part of this thread's 4 x 8 block
 #pragma unroll
     for (int a = 0; a < 4; ++a) {
       const int gi = bi * kBlk + ti * 4 + a;
       if (gi >= N) continue;
       int32_t* row = acc + 2 * (static_cast<long long>(c) * nbl + static_cast<long long>(gi) * (gi + 1) / 2);
 #pragma unroll
-      for (int b = 0; b < 4; ++b) {
-        const int gj = bj * kBlk + tj * 4 + b;
+      for (int b = 0; b < 8; ++b) {
+        const int gj = bj * kBlk + (b >> 2) * 32 + tj * 4 + (b & 3);
         if (gj > gi) continue;
         int2* dst = reinterpret_cast<int2*>(row + 2 * gj);
         if (!debug_in_bounds(dst, reinterpret_cast<int2*>(acc), C * nbl, err)) continue;

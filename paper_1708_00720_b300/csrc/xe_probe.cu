@@ -2,12 +2,15 @@
 // arithmetic ceiling of the plain int32 comparison kernel (xe_cudacore.cu),
 // whose inner loop is one dp4a per complex multiply-accumulate.
 //
-// Every thread runs 8 independent dp4a chains (enough to cover the
-// instruction's latency at 32 warps per SM) on register operands; each chain
-// feeds its sum back in as the multiplied operand, so no step can be folded
-// away, and the loop is bound by dp4a issue alone.  Thread 0 of each CTA
-// records the clock64 cycles its CTA ran; every thread stores its sums so the
-// work cannot be removed.
+// Launched with one CTA per SM (the caller sizes the grid), so a CTA's
+// clock64 span is its SM's span and dp4a per SM per clock = the CTA's dp4a /
+// its span.  Every thread runs 8 independent dp4a chains on register
+// operands (8 warps x 8 chains per SM keep the pipe busy); each chain feeds
+// its sum back in as the multiplied operand, so no step can be folded away,
+// and the loop is bound by dp4a issue alone.  Thread 0 of each CTA records
+// the clock64 cycles its CTA ran; every thread stores its sums so the work
+// cannot be removed.  On B300 dp4a issues to the FMA-heavy pipe only, which
+// takes a warp instruction every other clock: 64 dp4a per SM per clock.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -20,7 +23,7 @@ namespace probe {
 constexpr int kChains = 8;
 constexpr int kUnroll = 32;
 
-__global__ void __launch_bounds__(256) dp4a_rate_kernel(int iters, long long* cycles, int* sink) {
+__global__ void __launch_bounds__(256, 1) dp4a_rate_kernel(int iters, long long* cycles, int* sink) {
   int a[kChains], acc[kChains];
   const int b = 0x01020304 ^ static_cast<int>(threadIdx.x);
 #pragma unroll

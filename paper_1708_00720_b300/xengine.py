@@ -226,8 +226,7 @@ def dp4a_rate_per_sm_clock(device=None, iters: int = 4096) -> float:
     (the arithmetic ceiling of the plain int32 X-engine)."""
     import torch
     dev = torch.device("cuda", torch.cuda.current_device()) if device is None else device
-    sms = torch.cuda.get_device_properties(dev).multi_processor_count
-    ctas = 4 * sms                      # 4 x 256 threads = 32 warps per SM
+    ctas = torch.cuda.get_device_properties(dev).multi_processor_count   # one CTA per SM
     cycles = torch.zeros(ctas, dtype=torch.int64, device=dev)
     sink = torch.zeros(ctas * 256, dtype=torch.int32, device=dev)
     per = ctypes.c_longlong()
@@ -235,8 +234,8 @@ def dp4a_rate_per_sm_clock(device=None, iters: int = 4096) -> float:
         _check(_lib.xe_probe_dp4a_rate(iters, ctas, cycles.data_ptr(), sink.data_ptr(),
                                        ctypes.byref(per), _stream(None)), "xe_probe_dp4a_rate")
     torch.cuda.synchronize(dev)
-    # 4 co-resident CTAs share an SM: its rate is 4 CTAs' dp4a over their span
-    return 4.0 * per.value / float(cycles.double().median())
+    # each SM ran one CTA: its rate is that CTA's dp4a over its span
+    return per.value / float(cycles.double().median())
 
 
 def status_of(fn, *args) -> int:
