@@ -51,6 +51,7 @@ SERVE_METRIC = ("streaming X-engine service, 3 streams: sustained aggregate cMAC
                 "and gulp-to-visibility latency p50/p99")
 CALIB_METRIC = "gain-calibration chi^2 + adjoint gradient: visibility baselines per second"
 METRIC = "X-engine complex-MAC TOPS & % FP8 peak at 512 inputs vs plain int32 kernel"
+L2_BYTES = 126 * 10**6   # B300 L2
 KERNEL_SOURCES = {
     "xcorr_tc_fp8": ["paper_1708_00720_b300/csrc/xe_tc8.cu", "paper_1708_00720_b300/csrc/xe_ptx.cuh"],
     "xcorr_tc_fp16": ["paper_1708_00720_b300/csrc/xe_tc8.cu", "paper_1708_00720_b300/csrc/xe_ptx.cuh"],
@@ -872,7 +873,13 @@ def run_ours(args):
     torch.cuda.synchronize(dev)
     eng.check()
 
-    # ---- timed region: K steps, CUDA events, clocks sampled meanwhile
+    # ---- timed region: K steps, CUDA events, clocks sampled meanwhile.  A
+    # gulp smaller than L2 (the tiny workload) would stay cached between
+    # steps: L2 is flushed (a 256 MiB write) before every step and the step
+    # time is the sum of the per-step events, flushes excluded; the flush
+    # also covers the host's submission of the next step.
+    small = x.nbytes < L2_BYTES
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev) if small else None
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True),
            torch.cuda.Event(enable_timing=True)) for _ in range(args.steps)]
     launches0 = xe.xe_plan_launch_count(eng.plan)
@@ -883,6 +890,8 @@ def run_ours(args):
         t_end = torch.cuda.Event(enable_timing=True)
         t_start.record(stream)
         for k in range(args.steps):
+            if small:
+                flush.fill_(k & 0xFF)
             ev[k][0].record(stream)
             eng.correlate_emit(gulp, vis, stream=stream)
             ev[k][1].record(stream)
@@ -894,6 +903,8 @@ def run_ours(args):
     eng.check()
     total_ms = t_start.elapsed_time(t_end)
     kern_all = sorted(e[0].elapsed_time(e[1]) for e in ev)
+    if small:
+        total_ms = sum(kern_all)
     kern_ms = statistics.mean(kern_all)
     kern_stats = {"median": statistics.median(kern_all), "best": kern_all[0],
                   "p90": kern_all[min(len(kern_all) - 1, int(0.9 * len(kern_all)))]}
@@ -1067,7 +1078,9 @@ def run_ours(args):
             "config": {"workload": WORKLOADS[wl][1] + (f" (channels overridden: {C})" if args.nchan else ""),
                        "n_input": N, "n_chan": C, "ntime": T,
                        "operand": args.operand, "output": "ci32 packed lower triangle",
-                       "l2": "inputs (%d MiB) exceed L2 (126 MB); no flush" % (x.nbytes >> 20),
+                       "l2": ("inputs (%d MiB) exceed L2 (126 MB); no flush" % (x.nbytes >> 20)) if not small
+                             else ("inputs (%d KiB) fit in L2: L2 flushed (256 MiB write) before every step; "
+                                   "step time = sum of per-step CUDA events, flushes excluded" % (x.nbytes >> 10)),
                        "parallelism": f"weak, {world} independent gulps"},
             "pct_fp8_peak": (100.0 * achieved / (2 * peaks["bf16"])) if args.operand != "int32" else None,
             "step_tflops": 8 * step_cmac * world / (ms * 1e-3) / 1e12,
