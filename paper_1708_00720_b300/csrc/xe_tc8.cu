@@ -1304,6 +1304,12 @@ xcorr_tc8_kernel(const __grid_constant__ PairLaunch<NP> L) {
         const long long wlen = w.lo < 0 ? P.acc_pairs : L.ws_pairs;
         // a tile strictly below the diagonal and inside N needs no checks
         const bool full = !t.transposed && t.ti > t.tj && t.ti * kTile + kTile <= P.N;
+        // A diagonal tile inside N, by 32 x 32 blocks: this warp's rows are
+        // inputs [32 quad, 32 quad + 32) of the tile and column chunk b holds
+        // inputs [32 b, 32 b + 32), so chunks b < quad lie wholly below the
+        // diagonal (written without checks), b > quad wholly above it
+        // (nothing to write) and only b == quad needs the per-element test.
+        const bool diag_in = !t.transposed && t.ti == t.tj && t.ti * kTile + kTile <= P.N;
         const bool tfull = t.transposed && t.tj * kTile + kTile <= P.N;
         const int gI = t.ti * kTile + il;           // this lane's row input
         const int* ro = s.rowoff + 32 * quad;
@@ -1317,13 +1323,16 @@ xcorr_tc8_kernel(const __grid_constant__ PairLaunch<NP> L) {
             stage_raw(sim, va, lane);
           }
           __syncwarp();
-          if (!t.transposed) {
+          if (diag_in && b > quad) {
+            // above the diagonal: nothing of this chunk is written
+          } else if (!t.transposed) {
             // 32 rows x 32 baselines: each row is 256 contiguous bytes (lanes
             // permuted); row r's corrections come from lane r
             const int gj = t.tj * kTile + col_to_input<EB>(cc + lane);
             const float cre = s.colcorr[cc + lane], cim = s.colcorr[kTile + cc + lane];
             int2* accj = acc + gj;
-            if (full && !accumulate) {
+            const bool unchecked = full || (diag_in && b < quad);
+            if (unchecked && !accumulate) {
 #pragma unroll 4
               for (int r = 0; r < 32; ++r) {
                 const float rre = __shfl_sync(0xFFFFFFFFu, row_re, r), rim = __shfl_sync(0xFFFFFFFFu, row_im, r);
@@ -1331,7 +1340,7 @@ xcorr_tc8_kernel(const __grid_constant__ PairLaunch<NP> L) {
                 if (debug_in_bounds(dst, wbase, wlen, P.err))
                   *dst = unbias<EB>(staged(sb, r, lane), rre, rim, cre, cim);
               }
-            } else if (full) {
+            } else if (unchecked) {
 #pragma unroll 4
               for (int r = 0; r < 32; ++r) {
                 const float rre = __shfl_sync(0xFFFFFFFFu, row_re, r), rim = __shfl_sync(0xFFFFFFFFu, row_im, r);
