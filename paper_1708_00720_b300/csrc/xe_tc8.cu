@@ -1333,12 +1333,21 @@ xcorr_tc8_kernel(const __grid_constant__ PairLaunch<NP> L) {
             int2* accj = acc + gj;
             const bool unchecked = full || (diag_in && b < quad);
             if (unchecked && !accumulate) {
-#pragma unroll 4
-              for (int r = 0; r < 32; ++r) {
-                const float rre = __shfl_sync(0xFFFFFFFFu, row_re, r), rim = __shfl_sync(0xFFFFFFFFu, row_im, r);
-                int2* dst = accj + ro[r];
-                if (debug_in_bounds(dst, wbase, wlen, P.err))
-                  *dst = unbias<EB>(staged(sb, r, lane), rre, rim, cre, cim);
+              // row r's offset comes from lane r by shuffle, and the staged
+              // values of 8 rows are read before their 8 stores
+              const int rof = ro[lane];
+#pragma unroll 1
+              for (int r0 = 0; r0 < 32; r0 += 8) {
+                int2 sv[8];
+#pragma unroll
+                for (int q = 0; q < 8; ++q) sv[q] = staged(sb, r0 + q, lane);
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                  const int r = r0 + q;
+                  const float rre = __shfl_sync(0xFFFFFFFFu, row_re, r), rim = __shfl_sync(0xFFFFFFFFu, row_im, r);
+                  int2* dst = accj + __shfl_sync(0xFFFFFFFFu, rof, r);
+                  if (debug_in_bounds(dst, wbase, wlen, P.err)) *dst = unbias<EB>(sv[q], rre, rim, cre, cim);
+                }
               }
             } else if (unchecked) {
 #pragma unroll 4
