@@ -1278,10 +1278,11 @@ xcorr_tc8_kernel(const __grid_constant__ PairLaunch<NP> L) {
         tmem_ld32(t_row + 64, va);
         tmem_ld32(t_row + 96, vb);
         tmem_ld_wait();
-        stage_raw(sre + 2 * kStageChunk, va, lane);
+        // D_re is in registers and staging: release it before staging chunk 2
         tc_fence_before();
         __syncwarp();
         if (lane == 0) arrive_relaxed_at(s.acc_empty, 0);
+        stage_raw(sre + 2 * kStageChunk, va, lane);
 #pragma unroll 1
         for (int b = 0; b < 4; ++b) {
           tmem_ld32(t_row + 128 + 32 * b, va);
