@@ -137,7 +137,7 @@ struct StreamImpl {
   bool integ_has_data = false;       // a launch with accumulate = 0 has been made for it
   bool emit_pending = false;         // integration complete, waiting to be emitted
   long long emit_index = 0;
-  bool flush_requested = false;
+  long long flush_seq = -1;          // gulps up to this one have been flushed
   long long last_seq = -1;
   std::deque<std::unique_ptr<Emit>> emits;   // emitted, in order (ready or not)
   std::deque<std::unique_ptr<Emit>> handed;  // returned by poll, output slot not yet released
@@ -436,10 +436,12 @@ void maybe_close(StreamImpl* s) {
   for (const Gulp& gp : s->pending)
     if (gp.seq / G == s->integ_index) pend_same = true;
   const bool later_seen = s->last_seq > last_of_integ;   // the writer has moved past it
-  if (!pend_same && (s->integ_gulps == G || later_seen || s->flush_requested)) {
+  // a flush closes the integration that holds the gulps committed before it
+  // (one that comes later is not affected)
+  const bool flushed = s->flush_seq >= s->integ_index * G;
+  if (!pend_same && (s->integ_gulps == G || later_seen || flushed)) {
     s->emit_pending = true;
     s->emit_index = s->integ_index;
-    s->flush_requested = false;
   }
 }
 
@@ -778,7 +780,7 @@ XE_API xe_status xe_service_flush(xe_service_t svc, int id) {
   std::lock_guard<std::mutex> lk(S.mu);
   StreamImpl* s = get_stream(&S, id);
   if (!s) return XE_ERR_INVALID_ARG;
-  s->flush_requested = true;
+  s->flush_seq = s->last_seq;
   pump_stream(s);
   S.cv.notify_all();
   return XE_OK;

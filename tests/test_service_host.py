@@ -129,6 +129,29 @@ def test_integration_boundaries_gaps_and_flush():
     assert s.stats(a)["integrations"] == 3
 
 
+def test_flush_with_nothing_open_does_not_cut_the_next_integration():
+    """A flush after an integration has already closed applies to nothing:
+    the next integration's first gulp must not be emitted alone (a stale
+    flush once closed it after one gulp and emitted the rest a second time
+    under the same index)."""
+    s = mk(manual=False)
+    a = s.add_stream(16, 16, 4, ring_gulps=8, integrate_gulps=4, guaranteed=True)
+    for q in range(4):
+        put(s, a, q)
+    r = s.poll(a)
+    assert (r["index"], r["gulps"]) == (0, 4)
+    s.release(a, 0)
+    s.flush(a)                                      # integration 0 is already out
+    put(s, a, 4)
+    assert s.poll(a) is None                        # integration 1 stays open
+    for q in (5, 6, 7):
+        put(s, a, q)
+    r = s.poll(a)
+    assert (r["index"], r["first_seq"], r["gulps"], r["skipped"]) == (1, 4, 4, 0)
+    s.release(a, 1)
+    assert s.stats(a)["integrations"] == 2
+
+
 def test_sequence_numbers_must_increase():
     s = mk(manual=False)
     a = s.add_stream(16, 16, 4, ring_gulps=4, integrate_gulps=4)
