@@ -14,7 +14,11 @@
 //   device ring               [R][T][C][N]  (H2D copy of each committed slot)
 //   plan (int32 accumulator), device visibility buffer, two pinned output slots
 //   three CUDA streams: H2D copies, compute (correlate, integrate), D2H copies
-// A committed gulp is copied to its device slot at once.  The dispatcher
+// Host-link copies (a committed gulp into its device slot, an integration's
+// visibilities out) go in 32 MB pieces, at most 4 in flight per direction,
+// the streams' queued copies taking turns, so that a small stream's copy does
+// not wait behind a large one's (copies of one direction run in submission
+// order); a gulp is dispatched once its last piece has been issued.  The dispatcher
 // launches the correlation of every pending gulp that is contiguous in the
 // ring and belongs to the current integration as ONE launch, as soon as the
 // stream has fewer than two launches in flight and the GPU fewer than two in
@@ -36,6 +40,7 @@
 // the dry-run work stays "in flight" until xe_service_dryrun_complete.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <atomic>
 #include <chrono>
 #include <condition_variable>
@@ -70,6 +75,20 @@ constexpr int kMaxInflight = 2;  // correlate launches in flight per stream
 #define XE_SVC_INFLIGHT_TOTAL 2
 #endif
 constexpr int kMaxInflightTotal = XE_SVC_INFLIGHT_TOTAL;
+// Host-link copies go out in pieces, a bounded number in flight per
+// direction and the streams taking turns: a GPU runs the copies of one
+// direction in submission order, so a 1 GB visibility copy issued whole
+// would hold a small stream's copy back for ~20 ms.  A piece's completion
+// is an event the worker polls (a host callback per piece would hold its
+// CUDA stream until it had run, leaving gaps between pieces).
+#ifndef XE_SVC_COPY_PIECE_MB
+#define XE_SVC_COPY_PIECE_MB 32
+#endif
+#ifndef XE_SVC_COPY_PIECES
+#define XE_SVC_COPY_PIECES 4
+#endif
+constexpr size_t kCopyPiece = size_t(XE_SVC_COPY_PIECE_MB) << 20;
+constexpr int kPiecesInFlight = XE_SVC_COPY_PIECES;
 
 enum SlotState : int { kFree = 0, kReserved, kCommitted, kDispatched };
 
@@ -77,7 +96,8 @@ struct Gulp {
   long long seq;
   int slot;
   double t_commit;
-  cudaEvent_t h2d_done;   // recorded after the slot's H2D copy (real mode)
+  cudaEvent_t h2d_done;   // recorded after the slot's last H2D piece (real mode)
+  bool h2d_issued;        // every piece of its H2D copy has been issued
 };
 
 struct Batch {
@@ -107,6 +127,16 @@ struct Emit {
 
 struct ServiceImpl;
 
+// One host-link copy, issued piece by piece by pump_copies: a gulp into its
+// ring slot (H2D) or an integration's visibilities out (D2H).
+struct CopyJob {
+  uint8_t* dst = nullptr;
+  const uint8_t* src = nullptr;
+  size_t bytes = 0, issued = 0;
+  long long gulp_seq = -1;   // H2D: the gulp it carries
+  Emit* emit = nullptr;      // D2H: the integration it delivers
+};
+
 struct StreamImpl {
   int id = 0;
   xe_stream_config cfg{};
@@ -122,6 +152,8 @@ struct StreamImpl {
   bool out_busy[kOutSlots] = {false, false};
   cudaStream_t s_h2d = nullptr, s_comp = nullptr, s_d2h = nullptr;
   cudaEvent_t d2h_done = nullptr;   // last D2H out of d_vis
+  std::deque<std::unique_ptr<CopyJob>> copies[2];   // H2D, D2H jobs of this stream, in order
+  bool d2h_open = false;            // a D2H job out of d_vis still has pieces to issue
   // ring state
   std::vector<int> slot_state;
   std::vector<cudaEvent_t> slot_event;
@@ -164,6 +196,10 @@ struct ServiceImpl {
   std::thread worker;
   bool stop = false;
   std::string last_error;
+  // per direction (H2D, D2H): the events of the pieces in flight, oldest
+  // first, and the stream whose job goes next
+  std::deque<cudaEvent_t> pieces[2];
+  int copy_turn[2] = {0, 0};
 };
 
 struct HostCbBatch {
@@ -178,6 +214,7 @@ struct HostCbShared {
   std::vector<Batch*> b;
   ServiceImpl* svc;
 };
+
 
 void CUDART_CB on_batch_done(void* p) {
   auto* h = static_cast<HostCbBatch*>(p);
@@ -218,6 +255,87 @@ void retire(StreamImpl* s) {
   }
 }
 
+// Issue copy pieces while fewer than kPiecesInFlight of a direction are in
+// flight, the streams with queued jobs taking turns (a stream's own jobs go
+// in order, on its own CUDA stream).  A job's last piece records what waits
+// for it: for a gulp, the event its correlation waits on (the gulp becomes
+// dispatchable); for an integration, d2h_done and the callback that hands it
+// to the consumer.
+void pump_copies(ServiceImpl* svc) {
+  const int ns = static_cast<int>(svc->streams.size());
+  if (svc->dry || ns == 0) return;
+  for (int dir = 0; dir < 2; ++dir) {
+    // retire the pieces that have landed (in order: one engine per direction)
+    while (!svc->pieces[dir].empty()) {
+      const cudaError_t q = cudaEventQuery(svc->pieces[dir].front());
+      if (q == cudaErrorNotReady) break;
+      if (q != cudaSuccess) cudaGetLastError();
+      cudaEventDestroy(svc->pieces[dir].front());
+      svc->pieces[dir].pop_front();
+    }
+    int idle = 0;
+    while (idle < ns && static_cast<int>(svc->pieces[dir].size()) < kPiecesInFlight) {
+      const int turn = svc->copy_turn[dir] % ns;
+      svc->copy_turn[dir] = (turn + 1) % ns;
+      StreamImpl* s = svc->streams[turn].get();
+      if (s->copies[dir].empty()) {
+        ++idle;
+        continue;
+      }
+      idle = 0;
+      CopyJob* j = s->copies[dir].front().get();
+      cudaStream_t cs = dir == 0 ? s->s_h2d : s->s_d2h;
+      const size_t n = std::min(kCopyPiece, j->bytes - j->issued);
+      bool ok = cudaMemcpyAsync(j->dst + j->issued, j->src + j->issued, n,
+                                dir == 0 ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToHost, cs) == cudaSuccess;
+      if (ok) {
+        cudaEvent_t pe = nullptr;
+        ok = cudaEventCreateWithFlags(&pe, cudaEventDisableTiming) == cudaSuccess &&
+             cudaEventRecord(pe, cs) == cudaSuccess;
+        if (ok) {
+          svc->pieces[dir].push_back(pe);
+        } else if (pe) {
+          cudaEventDestroy(pe);
+        }
+      }
+      j->issued += n;
+      if (ok && j->issued < j->bytes) continue;
+      // the job's last piece has been issued (or a piece failed)
+      if (dir == 0) {
+        for (Gulp& g : s->pending) {
+          if (g.seq != j->gulp_seq) continue;
+          if (ok) ok = cudaEventRecord(g.h2d_done, cs) == cudaSuccess;
+          g.h2d_issued = true;
+          break;
+        }
+        if (!ok) {
+          cudaGetLastError();
+          fail_stream(s, XE_ERR_CUDA, "H2D copy failed");
+        }
+      } else {
+        Emit* e = j->emit;
+        if (ok) ok = cudaEventRecord(s->d2h_done, cs) == cudaSuccess;
+        if (ok) {
+          auto* cb = new HostCbEmit{e, svc};
+          if (cudaLaunchHostFunc(cs, on_emit_done, cb) != cudaSuccess) {
+            delete cb;
+            ok = false;
+          }
+        }
+        if (!ok) {
+          cudaGetLastError();
+          e->status = XE_ERR_CUDA;
+          e->t_done = now_ms();
+          e->ready.store(1, std::memory_order_release);
+          fail_stream(s, XE_ERR_CUDA, "D2H copy failed");
+        }
+        s->d2h_open = false;
+      }
+      s->copies[dir].pop_front();
+    }
+  }
+}
+
 int free_out_slot(StreamImpl* s) {
   for (int k = 0; k < kOutSlots; ++k)
     if (!s->out_busy[k]) return k;
@@ -227,6 +345,7 @@ int free_out_slot(StreamImpl* s) {
 // Emit the accumulator of the current integration into a free output slot.
 // Returns false if no output slot is free (the emit stays pending).
 bool try_emit(StreamImpl* s) {
+  if (s->d2h_open) return false;   // the previous copy out of d_vis still has pieces to issue
   const int slot = free_out_slot(s);
   if (slot < 0) return false;
   auto e = std::make_unique<Emit>();
@@ -258,18 +377,18 @@ bool try_emit(StreamImpl* s) {
     cudaEvent_t ev;
     cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
     cudaEventRecord(ev, s->s_comp);
-    cudaStreamWaitEvent(s->s_d2h, ev, 0);
+    cudaStreamWaitEvent(s->s_d2h, ev, 0);   // the pieces, issued later on s_d2h, follow it
     cudaEventDestroy(ev);
-    cudaMemcpyAsync(s->h_out[slot], s->d_vis, s->vis_bytes, cudaMemcpyDeviceToHost, s->s_d2h);
-    cudaEventRecord(s->d2h_done, s->s_d2h);
-    const cudaError_t ce = cudaLaunchHostFunc(s->s_d2h, on_emit_done, new HostCbEmit{raw, s->svc});
-    if (st != XE_OK || ce != cudaSuccess) {
-      raw->status = st != XE_OK ? st : XE_ERR_CUDA;
-      fail_stream(s, static_cast<xe_status>(raw->status), "emit failed");
-      if (ce != cudaSuccess) {
-        raw->t_done = now_ms();
-        raw->ready.store(1);
-      }
+    auto j = std::make_unique<CopyJob>();
+    j->dst = static_cast<uint8_t*>(s->h_out[slot]);
+    j->src = static_cast<const uint8_t*>(s->d_vis);
+    j->bytes = s->vis_bytes;
+    j->emit = raw;
+    s->copies[1].push_back(std::move(j));
+    s->d2h_open = true;
+    if (st != XE_OK) {
+      raw->status = st;
+      fail_stream(s, st, "emit failed");
     }
   }
   s->st.integrations++;
@@ -287,12 +406,14 @@ bool next_run(StreamImpl* s, Run* r) {
   if (s->state != XE_OK || s->pending.empty() || static_cast<int>(s->inflight.size()) >= kMaxInflight ||
       s->emit_pending || s->svc->inflight_total >= kMaxInflightTotal)
     return false;
+  if (!s->pending.front().h2d_issued) return false;   // its copy is still being issued
   const int G = s->cfg.integrate_gulps;
   const long long integ = s->pending.front().seq / G;
   if (s->integ_index >= 0 && integ != s->integ_index) return false;   // previous integration not emitted yet
   int n = 1;
   while (n < static_cast<int>(s->pending.size()) && s->pending[n].seq / G == integ &&
-         s->pending[n].slot == s->pending[n - 1].slot + 1)   // contiguous, no wrap
+         s->pending[n].slot == s->pending[n - 1].slot + 1 &&   // contiguous, no wrap
+         s->pending[n].h2d_issued)
     ++n;
   r->first = s->pending.front().slot;
   r->n = n;
@@ -465,6 +586,7 @@ void pump_stream(StreamImpl* s) {
 }
 
 void pump_all(ServiceImpl* svc) {
+  pump_copies(svc);
   // close and emit finished integrations first, so that their streams can
   // take part in a shared launch of the next gulps
   for (auto& s : svc->streams) {
@@ -474,13 +596,16 @@ void pump_all(ServiceImpl* svc) {
   }
   if (svc->batch) dispatch_shared(svc);
   for (auto& s : svc->streams) pump_stream(s.get());
+  pump_copies(svc);   // copies of integrations emitted just now
 }
 
 void worker_loop(ServiceImpl* svc) {
   std::unique_lock<std::mutex> lk(svc->mu);
   while (!svc->stop) {
     pump_all(svc);
-    svc->cv.wait_for(lk, std::chrono::microseconds(500));
+    // with copy pieces in flight the worker polls their events more often
+    const bool copying = !svc->pieces[0].empty() || !svc->pieces[1].empty();
+    svc->cv.wait_for(lk, std::chrono::microseconds(copying ? 100 : 500));
   }
 }
 
@@ -607,6 +732,8 @@ XE_API xe_status xe_service_destroy(xe_service_t svc) {
   if (S.worker.joinable()) S.worker.join();
   if (S.s_batch) cudaStreamSynchronize(S.s_batch);   // shared launches read every stream's ring
   for (auto& s : S.streams) free_stream_resources(s.get(), S.dry);
+  for (auto& q : S.pieces)
+    for (cudaEvent_t e : q) cudaEventDestroy(e);
   if (S.s_batch) cudaStreamDestroy(S.s_batch);
   delete svc;
   return XE_OK;
@@ -737,18 +864,21 @@ XE_API xe_status xe_service_commit(xe_service_t svc, int id, long long seq) {
     pump_stream(s);
     return XE_OK;
   }
-  Gulp g{seq, slot, now_ms(), nullptr};
+  Gulp g{seq, slot, now_ms(), nullptr, S.dry};
   if (!S.dry) {
-    const size_t off = static_cast<size_t>(slot) * s->gulp_bytes;
-    bool ok = cudaMemcpyAsync(s->d_ring + off, s->h_ring + off, s->gulp_bytes, cudaMemcpyHostToDevice, s->s_h2d) ==
-              cudaSuccess;
-    ok = ok && cudaEventCreateWithFlags(&g.h2d_done, cudaEventDisableTiming) == cudaSuccess;
-    ok = ok && cudaEventRecord(g.h2d_done, s->s_h2d) == cudaSuccess;
-    if (!ok) {
+    if (cudaEventCreateWithFlags(&g.h2d_done, cudaEventDisableTiming) != cudaSuccess) {
       cudaGetLastError();
       unreserve();
       return fail_stream(s, XE_ERR_CUDA, "H2D copy failed");
     }
+    // the copy goes out in pieces (pump_copies, below)
+    const size_t off = static_cast<size_t>(slot) * s->gulp_bytes;
+    auto j = std::make_unique<CopyJob>();
+    j->dst = s->d_ring + off;
+    j->src = s->h_ring + off;
+    j->bytes = s->gulp_bytes;
+    j->gulp_seq = seq;
+    s->copies[0].push_back(std::move(j));
   }
   s->slot_state[slot] = kCommitted;
   s->reserved_slot = -1;
