@@ -285,7 +285,8 @@ void pump_copies(ServiceImpl* svc) {
       idle = 0;
       CopyJob* j = s->copies[dir].front().get();
       cudaStream_t cs = dir == 0 ? s->s_h2d : s->s_d2h;
-      const size_t n = std::min(kCopyPiece, j->bytes - j->issued);
+      // with one stream there is nobody to take turns with: the whole copy
+      const size_t n = ns == 1 ? j->bytes - j->issued : std::min(kCopyPiece, j->bytes - j->issued);
       bool ok = cudaMemcpyAsync(j->dst + j->issued, j->src + j->issued, n,
                                 dir == 0 ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToHost, cs) == cudaSuccess;
       if (ok) {
