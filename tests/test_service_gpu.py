@@ -176,3 +176,32 @@ def test_serving_workload_shapes_bit_exact(sv):
     print("\nlaunches shared between streams:", [s.stats(sid)["shared_launches"] for sid in ids],
           "of", [s.stats(sid)["launches"] for sid in ids])
     s.close()
+
+
+def test_small_stream_is_not_held_behind_a_large_copy(sv):
+    """Host-link copies of one direction run in submission order, so the
+    service issues them in pieces with the streams taking turns: a small
+    stream's integration, emitted just after a large stream's 1 GB
+    visibility copy has started, must come back long before that copy ends
+    (whole copies kept it waiting for all of it).  Both stay bit-exact."""
+    big, small = (1024, 256, 64), (64, 8, 64)
+    s = sv.Service()
+    a = s.add_stream(*big, ring_gulps=2, integrate_gulps=1, guaranteed=True)
+    b = s.add_stream(*small, ring_gulps=2, integrate_gulps=1, guaranteed=True)
+    ga = gulps_for(*big, 2, seed=90)
+    gb = gulps_for(*small, 2, seed=91)
+    lat = {a: [], b: []}
+    for q in range(2):
+        assert s.submit(a, ga[q], q, timeout_ms=20000)
+        time.sleep(0.002)                           # the large copy is under way
+        assert s.submit(b, gb[q], q, timeout_ms=20000)
+        for sid, gl, chans in ((b, gb, np.arange(8)), (a, ga, np.array([0, 255]))):
+            r = s.poll(sid, timeout_ms=60000)
+            assert r is not None and r["status"] == 0 and r["index"] == q
+            x = gl[q]
+            np.testing.assert_array_equal(r["vis"][chans], oracle.correlate(np.ascontiguousarray(x[:, chans, :])))
+            lat[sid].append(r["latency_ms"])
+            s.release(sid, q)
+    s.close()
+    print("\nlatency ms: large", [round(v, 1) for v in lat[a]], "small", [round(v, 1) for v in lat[b]])
+    assert max(lat[b]) < 0.5 * min(lat[a]), lat
