@@ -310,7 +310,9 @@ XE_API xe_status xe_calib_scale(xe_calib_t calib, const float *d_in, const doubl
  * staging ring, fills it with one gulp uint8[gulp_ntime][n_chan][n_input],
  * and commits it with its sequence number (strictly increasing; gaps are
  * gulps that never arrived).  Committed gulps are copied to the device ring
- * at once; pending gulps that are contiguous in the ring are correlated in
+ * in 32 MB pieces, at most 4 in flight per direction with the streams
+ * taking turns (whole when the service has one stream); pending gulps whose
+ * copies are issued and that are contiguous in the ring are correlated in
  * one launch whenever the stream has fewer than two launches in flight and
  * the GPU fewer than two in all (an idle GPU takes a gulp at once; a busy
  * one lets ready gulps gather).
@@ -321,7 +323,8 @@ XE_API xe_status xe_calib_scale(xe_calib_t calib, const float *d_in, const doubl
  * XE_SERVICE_NO_BATCH keeps every launch to one stream.
  * Integration k covers sequence numbers [k G, (k+1) G), G = integrate_gulps;
  * it is emitted when its last gulp has been correlated, when a later gulp is
- * committed, or on flush, into one of two pinned output buffers per stream
+ * committed, or on flush (which closes the integration holding the gulps
+ * committed before it), into one of two pinned output buffers per stream
  * that the consumer gets from xe_service_poll and hands back with
  * xe_service_release.  Ring full: a guaranteed stream makes reserve wait (up
  * to timeout_ms; back-pressure), an unguaranteed one returns XE_ERR_BUSY at

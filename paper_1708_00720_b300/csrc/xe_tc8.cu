@@ -65,7 +65,9 @@
 //    D_im is still being read); then the bias is removed exactly from per-input
 //    sums of u (the column sums of the other half of J are read from the
 //    partner's shared memory) and rows are written coalesced to the
-//    accumulator:
+//    accumulator (8 staged rows read before their stores, row and column
+//    values shuffled from the lanes holding them, diagonal tiles by 32 x 32
+//    blocks: unchecked below the diagonal, skipped above it):
 //      Re V = D_re - 8 (P_i + Q_i + P_j + Q_j) + 128 T'
 //      Im V = D_im + 8 (P_i - Q_i) - 8 (P_j - Q_j).
 // Exactness: all partial sums of D stay below 450 T' <= 2^24 for T' <= 37282;
